@@ -1,0 +1,246 @@
+"""FP64 CPU oracle for the TAGI convolution sums and the Green step.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+benchmark's CPU-baseline leg, never by the product path.  It shares no code
+with the CUDA library.  The arithmetic lives in ``oracle.c`` (direct sums,
+tree, Algorithm 3 treecode, anterpolation); this module loads it with ctypes
+and adds the Green step of Algorithm 2 in plain NumPy.
+
+Parity pins: every function here is checked in ``tests/test_oracle_*.py``
+against closed forms, invariants and brute force (see each test's docstring).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_I32 = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, -ffp-contract=off)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
+                               "-ffp-contract=off", "-o", _SO, _SRC, "-lm"])
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        L.oracle_direct_yukawa.argtypes = [ctypes.c_int64, _D, _D, _D, _D, ctypes.c_int64, _D, _D,
+                                           _D, _D, _D, ctypes.c_double, ctypes.c_int, _D]
+        L.oracle_direct_coulomb.argtypes = L.oracle_direct_yukawa.argtypes
+        L.oracle_tree_build.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int]
+        L.oracle_tree_build.restype = ctypes.c_void_p
+        L.oracle_tree_free.argtypes = [ctypes.c_void_p]
+        L.oracle_tree_num_clusters.argtypes = [ctypes.c_void_p]
+        L.oracle_tree_export.argtypes = [ctypes.c_void_p, _I64, _I64, _I64, _D, _D, _I32, _I32,
+                                         _I32, _I32]
+        L.oracle_tree_lists.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_int64, _I32, _I32, _I32]
+        L.oracle_tree_lists.restype = ctypes.c_int64
+        L.oracle_cluster_proxies.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, _D, _D]
+        L.oracle_anterpolate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         _D, _D]
+        L.oracle_treecode.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, _D, _D, _D]
+        L.oracle_treecode_batches.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _D,
+                                              ctypes.c_int, _I32, _D]
+        _lib = L
+    return _lib
+
+
+def _p(a, t=_D):
+    return a.ctypes.data_as(t)
+
+
+def _c(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ---------------------------------------------------------------- direct sums
+def direct_yukawa(xyz, w, f, k, ss=True, targets=None):
+    """Eq. direct-sum with G_k = exp(-k r)/(4 pi r); SS per Eq. yukawa-conv-ss.
+
+    xyz (3, N), w (N,), f (N,).  targets: optional index array; the result
+    then holds those targets only (sources are always all N points)."""
+    xyz, w, f = _c(xyz), _c(w), _c(f)
+    ti = np.arange(xyz.shape[1]) if targets is None else np.asarray(targets)
+    t = _c(xyz[:, ti])
+    tf = _c(f[ti])
+    u = np.zeros(len(ti))
+    lib().oracle_direct_yukawa(len(ti), _p(t[0]), _p(t[1]), _p(t[2]), _p(tf), xyz.shape[1],
+                               _p(xyz[0]), _p(xyz[1]), _p(xyz[2]), _p(w), _p(f), float(k),
+                               int(ss), _p(u))
+    return u
+
+
+def direct_coulomb(xyz, w, rho, alpha=1.0, ss=True, targets=None):
+    """Eq. direct-sum with 1/r; SS per Eq. coulomb-conv-ss and correction_term."""
+    xyz, w, rho = _c(xyz), _c(w), _c(rho)
+    ti = np.arange(xyz.shape[1]) if targets is None else np.asarray(targets)
+    t = _c(xyz[:, ti])
+    tr = _c(rho[ti])
+    v = np.zeros(len(ti))
+    lib().oracle_direct_coulomb(len(ti), _p(t[0]), _p(t[1]), _p(t[2]), _p(tr), xyz.shape[1],
+                                _p(xyz[0]), _p(xyz[1]), _p(xyz[2]), _p(w), _p(rho), float(alpha),
+                                int(ss), _p(v))
+    return v
+
+
+# ---------------------------------------------------------------- treecode
+class Tree:
+    """Source-cluster tree of Section 5.1 (batches = leaves, N_B = N_L)."""
+
+    def __init__(self, xyz, leaf_size):
+        self.xyz = _c(xyz)
+        self.n = self.xyz.shape[1]
+        self.leaf_size = int(leaf_size)
+        self._h = lib().oracle_tree_build(self.n, _p(self.xyz[0]), _p(self.xyz[1]),
+                                          _p(self.xyz[2]), self.leaf_size)
+        if not self._h:
+            raise ValueError("oracle tree build rejected its arguments")
+        nc = lib().oracle_tree_num_clusters(self._h)
+        self.nc = nc
+        self.idx = np.empty(self.n, np.int64)
+        self.begin = np.empty(nc, np.int64)
+        self.end = np.empty(nc, np.int64)
+        self.lo = np.empty((nc, 3))
+        self.hi = np.empty((nc, 3))
+        self.parent = np.empty(nc, np.int32)
+        self.level = np.empty(nc, np.int32)
+        self.nchild = np.empty(nc, np.int32)
+        self.child = np.empty((nc, 8), np.int32)
+        lib().oracle_tree_export(self._h, _p(self.idx, _I64), _p(self.begin, _I64),
+                                 _p(self.end, _I64), _p(self.lo), _p(self.hi),
+                                 _p(self.parent, _I32), _p(self.level, _I32),
+                                 _p(self.nchild, _I32), _p(self.child, _I32))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().oracle_tree_free(self._h)
+            self._h = None
+
+    @property
+    def leaves(self):
+        return np.nonzero(self.nchild == 0)[0]
+
+    def points(self, c):
+        return self.idx[self.begin[c]:self.end[c]]
+
+    def key(self, c):
+        """Order-free identity of a cluster: (smallest point index, size)."""
+        pts = self.points(c)
+        return (int(pts.min()), int(len(pts)))
+
+    def lists(self, theta, degree):
+        """Algorithm 3's visits: arrays batch, cluster, kind (0 direct, 1 approx)."""
+        cap = 1 << 16
+        while True:
+            b = np.empty(cap, np.int32)
+            c = np.empty(cap, np.int32)
+            k = np.empty(cap, np.int32)
+            cnt = lib().oracle_tree_lists(self._h, float(theta), int(degree), cap, _p(b, _I32),
+                                          _p(c, _I32), _p(k, _I32))
+            if cnt <= cap:
+                return b[:cnt], c[:cnt], k[:cnt]
+            cap = int(cnt)
+
+    def proxies(self, c, degree):
+        P = (degree + 1) ** 3
+        px, py, pz = np.empty(P), np.empty(P), np.empty(P)
+        lib().oracle_cluster_proxies(self._h, int(c), int(degree), _p(px), _p(py), _p(pz))
+        return np.stack([px, py, pz])
+
+    def anterpolate(self, c, degree, q):
+        """Proxy weights of cluster c for charge rows q (nq, N) -> (nq, P)."""
+        q = _c(np.atleast_2d(q))
+        P = (degree + 1) ** 3
+        out = np.empty((q.shape[0], P))
+        lib().oracle_anterpolate(self._h, int(c), int(degree), q.shape[0], _p(q), _p(out))
+        return out
+
+    def treecode(self, theta, degree, kernel, param, f, w, ss=True):
+        f, w = _c(f), _c(w)
+        u = np.empty(self.n)
+        rc = lib().oracle_treecode(self._h, float(theta), int(degree), int(kernel), float(param),
+                                   int(ss), _p(f), _p(w), _p(u))
+        if rc:
+            raise ValueError("oracle treecode rejected its arguments")
+        return u
+
+    def treecode_batches(self, theta, degree, kernel, param, f, w, batches, ss=True):
+        f, w = _c(f), _c(w)
+        b = _c(batches, np.int32)
+        u = np.zeros(self.n)
+        lib().oracle_treecode_batches(self._h, float(theta), int(degree), int(kernel),
+                                      float(param), int(ss), _p(f), _p(w), len(b), _p(b, _I32),
+                                      _p(u))
+        return u
+
+
+def treecode_yukawa(tree, theta, degree, f, k, w, ss=True):
+    return tree.treecode(theta, degree, 0, k, f, w, ss)
+
+
+def treecode_coulomb(tree, theta, degree, rho, w, alpha=1.0, ss=True):
+    return tree.treecode(theta, degree, 1, alpha, rho, w, ss)
+
+
+# ---------------------------------------------------------------- Green step
+def green_step(tree, theta, degree, w, veff, vshift, psi, eps, rho=None, alpha=1.0):
+    """One Green iteration for all orbitals (Algorithm 2 lines 3-6, batched).
+
+    Applies G(eps_o) to every orbital with its previous eigenvalue, updates each
+    eigenvalue by the gradient-free formula (Eq. gradient-free) using the
+    un-orthogonalised psi~, then orthonormalises the new orbitals by modified
+    Gram-Schmidt in index order under <a, b> = sum a b w.  The gauge shift of
+    Eq. gauge-shift enters as V + V_shift and k = sqrt(-2 (eps + V_shift));
+    the returned eigenvalues are unshifted.
+
+    Returns psi_new (nw, N), eps_new (nw,), resid (nw,) = ||psi_new - psi||_w,
+    and, when rho is given, V_H (N,) and E_H = 1/2 sum V_H rho w
+    (Eq. quadrature-example).
+    """
+    psi = np.atleast_2d(np.asarray(psi, np.float64))
+    eps = np.asarray(eps, np.float64)
+    nw = psi.shape[0]
+    vs = veff + vshift
+    es = eps + vshift
+    psi_t = np.empty_like(psi)
+    for o in range(nw):
+        k = np.sqrt(-2.0 * es[o])
+        u = treecode_yukawa(tree, theta, degree, vs * psi[o], k, w, ss=True)
+        psi_t[o] = -2.0 * u  # Eq. Yukawa: -1/(2 pi) = -2 * 1/(4 pi)
+    es_new = np.empty(nw)
+    for o in range(nw):
+        num = np.sum(vs * psi[o] * (psi[o] - psi_t[o]) * w)
+        den = np.sum(psi_t[o] * psi_t[o] * w)
+        es_new[o] = es[o] - num / den
+    q = np.empty_like(psi)
+    for o in range(nw):
+        v = psi_t[o].copy()
+        for p in range(o):
+            v -= np.sum(v * q[p] * w) * q[p]
+        q[o] = v / np.sqrt(np.sum(v * v * w))
+    resid = np.sqrt(np.sum((q - psi) ** 2 * w[None, :], axis=1))
+    out = {"psi": q, "eps": es_new - vshift, "resid": resid, "psi_tilde": psi_t}
+    if rho is not None:
+        vh = treecode_coulomb(tree, theta, degree, rho, w, alpha=alpha, ss=True)
+        out["vh"] = vh
+        out["eh"] = 0.5 * np.sum(vh * rho * w)
+    return out

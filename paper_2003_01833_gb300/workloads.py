@@ -1,0 +1,467 @@
+"""Seeded synthetic inputs for the TAGI convolution sums.
+
+This module builds the meshes, quadrature weights and fields that both the CUDA
+path and the oracle consume.  It holds none of the convolution arithmetic: only
+the discretisation of Section 3 (Chebyshev points of the first kind, Eq.
+Chebyshev_points; the Fejer rule; the adaptive refinement of Eq.
+refinement_criterion with the test function of Eq. test_function) and Slater-type
+stand-ins for the radial atomic data of Section 3.1, which is not available.
+
+Layout of every mesh: ``xyz`` is a float64 array of shape (3, N) (structure of
+arrays), ``w`` float64 (N,).  Fields are float64 arrays of shape (nf, N).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# Quadrature (Section 3.2)
+# --------------------------------------------------------------------------
+
+
+def chebyshev1_nodes(p: int) -> np.ndarray:
+    """Chebyshev points of the first kind on [-1, 1], Eq. Chebyshev_points:
+    x_i = cos((2i+1) pi / (2p+2)), i = 0..p."""
+    i = np.arange(p + 1)
+    return np.cos((2 * i + 1) * np.pi / (2 * p + 2))
+
+
+def fejer_weights(p: int) -> np.ndarray:
+    """Weights of Fejer's first rule on the p+1 first-kind Chebyshev points.
+
+    The paper cites the rule (Section 3.2) without printing it.  This is the
+    classical closed form: with N = p+1 points at angles t_i,
+    w_i = (2/N) [1 - 2 sum_{j=1}^{floor(N/2)} cos(2 j t_i) / (4 j^2 - 1)].
+    The rule integrates polynomials of degree <= p exactly on [-1, 1].
+    """
+    n = p + 1
+    t = (2 * np.arange(n) + 1) * np.pi / (2 * n)
+    s = np.zeros(n)
+    for j in range(1, n // 2 + 1):
+        s += np.cos(2 * j * t) / (4 * j * j - 1)
+    return (2.0 / n) * (1.0 - 2.0 * s)
+
+
+def cell_points(lo: np.ndarray, hi: np.ndarray, p: int):
+    """Tensor-product Fejer points and weights for M cuboid cells.
+
+    lo, hi: (M, 3).  Returns pts (M, (p+1)^3, 3) and wts (M, (p+1)^3).
+    Point order inside a cell: x slowest, z fastest.
+    """
+    x1 = chebyshev1_nodes(p)
+    w1 = fejer_weights(p)
+    c = 0.5 * (lo + hi)
+    h = 0.5 * (hi - lo)
+    X, Y, Z = np.meshgrid(x1, x1, x1, indexing="ij")
+    WX, WY, WZ = np.meshgrid(w1, w1, w1, indexing="ij")
+    ref = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)  # (P, 3)
+    wref = (WX * WY * WZ).ravel()  # (P,)
+    pts = c[:, None, :] + h[:, None, :] * ref[None, :, :]
+    wts = np.prod(h, axis=1)[:, None] * wref[None, :]
+    return pts, wts
+
+
+@dataclass
+class Mesh:
+    xyz: np.ndarray  # (3, N) float64
+    w: np.ndarray  # (N,) float64
+    cells_lo: np.ndarray  # (Nc, 3)
+    cells_hi: np.ndarray  # (Nc, 3)
+    p: int
+
+    @property
+    def n(self) -> int:
+        return self.w.shape[0]
+
+
+def mesh_from_cells(lo: np.ndarray, hi: np.ndarray, p: int) -> Mesh:
+    pts, wts = cell_points(lo, hi, p)
+    xyz = np.ascontiguousarray(pts.reshape(-1, 3).T)
+    return Mesh(xyz=xyz, w=np.ascontiguousarray(wts.ravel()), cells_lo=lo, cells_hi=hi, p=p)
+
+
+def uniform_mesh(lo: float, hi: float, ncell: int, p: int) -> Mesh:
+    """ncell^3 cubic cells on [lo, hi]^3 with (p+1)^3 Fejer points each."""
+    e = np.linspace(lo, hi, ncell + 1)
+    I, J, K = np.meshgrid(np.arange(ncell), np.arange(ncell), np.arange(ncell), indexing="ij")
+    idx = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1)
+    clo = e[idx]
+    chi = e[idx + 1]
+    return mesh_from_cells(clo, chi, p)
+
+
+# --------------------------------------------------------------------------
+# Slater-type atomic stand-ins (Section 3.1 uses radial Kohn-Sham data that is
+# not available; hydrogenic Slater functions replace it)
+# --------------------------------------------------------------------------
+
+# shells: (n, l, occupation, exponent zeta); radial part r^(n-1) e^{-zeta r} for
+# n=1 and the hydrogenic 2s form (2 - zeta r) e^{-zeta r/2}-like shapes below.
+ATOM_Z = {"H": 1, "Li": 3, "C": 6, "O": 8}
+
+
+def _shells(sym: str):
+    """Occupied shells of the neutral atom: list of (kind, occ, Z).
+
+    kind is '1s', '2s' or '2p'; the radial shapes are hydrogenic with the bare
+    nuclear charge, the stand-in the Li workload specifies (1s ~ e^{-Zr},
+    2s ~ (2 - Zr) e^{-Zr/2}); 2p ~ r e^{-Zr/2}.
+    """
+    Z = ATOM_Z[sym]
+    if sym == "H":
+        return [("1s", 1.0, Z)]
+    if sym == "Li":
+        return [("1s", 2.0, Z), ("2s", 1.0, Z)]
+    if sym == "C":
+        return [("1s", 2.0, Z), ("2s", 2.0, Z), ("2p", 2.0, Z)]
+    if sym == "O":
+        return [("1s", 2.0, Z), ("2s", 2.0, Z), ("2p", 4.0, Z)]
+    raise ValueError(sym)
+
+
+def radial_orbital(kind: str, Z: float, r: np.ndarray) -> np.ndarray:
+    """Normalised hydrogenic radial-times-angular-average orbital value."""
+    if kind == "1s":
+        return math.sqrt(Z**3 / math.pi) * np.exp(-Z * r)
+    if kind == "2s":
+        return math.sqrt(Z**3 / (32 * math.pi)) * (2.0 - Z * r) * np.exp(-0.5 * Z * r)
+    if kind == "2p":  # spherical average of |2p|^2 gives this amplitude
+        return math.sqrt(Z**5 / (96 * math.pi)) * r * np.exp(-0.5 * Z * r)
+    raise ValueError(kind)
+
+
+def atomic_density(sym: str, r: np.ndarray) -> np.ndarray:
+    rho = np.zeros_like(r)
+    for kind, occ, Z in _shells(sym):
+        rho += occ * radial_orbital(kind, Z, r) ** 2
+    return rho
+
+
+def _radial_hartree_table(sym: str, rmax: float = 80.0, m: int = 200001):
+    """Radial Hartree potential of the spherical atomic density on a fine
+    grid (Gauss's law: V(r) = Q(r)/r + 4 pi int_r^inf rho s ds)."""
+    s = np.linspace(0.0, rmax, m)
+    rho = atomic_density(sym, s)
+    f_in = 4 * np.pi * rho * s * s
+    f_out = 4 * np.pi * rho * s
+    ds = s[1] - s[0]
+    q = np.concatenate([[0.0], np.cumsum(0.5 * (f_in[1:] + f_in[:-1]) * ds)])
+    o = np.concatenate([[0.0], np.cumsum(0.5 * (f_out[1:] + f_out[:-1]) * ds)])
+    out = o[-1] - o
+    v = np.empty_like(s)
+    v[1:] = q[1:] / s[1:] + out[1:]
+    v[0] = out[0]
+    return s, v
+
+
+_VH_CACHE: dict = {}
+
+
+def atomic_hartree(sym: str, r: np.ndarray) -> np.ndarray:
+    if sym not in _VH_CACHE:
+        _VH_CACHE[sym] = _radial_hartree_table(sym)
+    s, v = _VH_CACHE[sym]
+    q_tot = sum(occ for _, occ, _ in _shells(sym))
+    out = np.interp(r, s, v)
+    far = r > s[-1]
+    out[far] = q_tot / r[far]
+    return out
+
+
+@dataclass
+class Molecule:
+    symbols: list
+    pos: np.ndarray  # (Na, 3)
+
+    @property
+    def Z(self) -> np.ndarray:
+        return np.array([ATOM_Z[s] for s in self.symbols], dtype=np.float64)
+
+
+def _dist(xyz: np.ndarray, R: np.ndarray) -> np.ndarray:
+    # xyz: (..., 3)
+    return np.sqrt(np.sum((xyz - R) ** 2, axis=-1))
+
+
+def density0(mol: Molecule, pts: np.ndarray) -> np.ndarray:
+    """Superposition of atomic densities, the form of Eq. initial_density."""
+    rho = np.zeros(pts.shape[:-1])
+    for s, R in zip(mol.symbols, mol.pos):
+        rho += atomic_density(s, _dist(pts, R))
+    return rho
+
+
+def v_ext(mol: Molecule, pts: np.ndarray) -> np.ndarray:
+    """External potential -sum_j Z_j/|r - R_j| (Eq. classical-electrostatics)."""
+    v = np.zeros(pts.shape[:-1])
+    for s, R in zip(mol.symbols, mol.pos):
+        v -= ATOM_Z[s] / _dist(pts, R)
+    return v
+
+
+def v_hartree0(mol: Molecule, pts: np.ndarray) -> np.ndarray:
+    v = np.zeros(pts.shape[:-1])
+    for s, R in zip(mol.symbols, mol.pos):
+        v += atomic_hartree(s, _dist(pts, R))
+    return v
+
+
+# --------------------------------------------------------------------------
+# Adaptive refinement (Section 3.2, Eq. refinement_criterion)
+# --------------------------------------------------------------------------
+
+
+def _children(lo: np.ndarray, hi: np.ndarray):
+    """Bisect each cell in the three coordinate directions: (8M, 3) arrays."""
+    mid = 0.5 * (lo + hi)
+    los, his = [], []
+    for code in range(8):
+        b = np.array([(code >> d) & 1 for d in range(3)], dtype=bool)
+        clo = np.where(b, mid, lo)
+        chi = np.where(b, hi, mid)
+        los.append(clo)
+        his.append(chi)
+    # child-major within each parent: shape (M, 8, 3)
+    return np.stack(los, axis=1).reshape(-1, 3), np.stack(his, axis=1).reshape(-1, 3)
+
+
+def _cell_integrals(fn, lo, hi, p, chunk=4096):
+    out = np.empty(lo.shape[0])
+    for s in range(0, lo.shape[0], chunk):
+        pts, wts = cell_points(lo[s : s + chunk], hi[s : s + chunk], p)
+        out[s : s + chunk] = np.sum(fn(pts) * wts, axis=1)
+    return out
+
+
+def _split_at_atoms(lo, hi, atoms, tol=1e-12):
+    """Final refinement: a cell holding an atom in its interior (or on a face
+    interior) is cut through the atom so the atom ends up at a vertex."""
+    changed = True
+    while changed:
+        changed = False
+        new_lo, new_hi = [], []
+        for a in atoms:
+            inside = np.all((lo <= a + tol) & (hi >= a - tol), axis=1)
+            strict = (lo < a - tol) & (hi > a + tol)  # (M, 3): dims to cut
+            need = inside & np.any(strict, axis=1)
+            if not np.any(need):
+                continue
+            changed = True
+            keep = ~need
+            for c in np.nonzero(need)[0]:
+                cuts = [[(lo[c, d], a[d]), (a[d], hi[c, d])] if strict[c, d] else [(lo[c, d], hi[c, d])] for d in range(3)]
+                for ix in cuts[0]:
+                    for iy in cuts[1]:
+                        for iz in cuts[2]:
+                            new_lo.append([ix[0], iy[0], iz[0]])
+                            new_hi.append([ix[1], iy[1], iz[1]])
+            lo, hi = lo[keep], hi[keep]
+        if new_lo:
+            lo = np.concatenate([lo, np.array(new_lo)])
+            hi = np.concatenate([hi, np.array(new_hi)])
+    return lo, hi
+
+
+def _fix_aspect(lo, hi, max_ratio=2.0):
+    """Cells with extent ratio above max_ratio are bisected along their
+    longest side until none remain (the paper's aspect-ratio refinement; the
+    threshold is not printed, 2 is this module's reading)."""
+    while True:
+        ext = hi - lo
+        ratio = ext.max(axis=1) / ext.min(axis=1)
+        bad = ratio > max_ratio
+        if not np.any(bad):
+            return lo, hi
+        d = np.argmax(ext[bad], axis=1)
+        blo, bhi = lo[bad].copy(), hi[bad].copy()
+        mid = 0.5 * (blo[np.arange(len(d)), d] + bhi[np.arange(len(d)), d])
+        a_lo, a_hi = blo.copy(), bhi.copy()
+        a_hi[np.arange(len(d)), d] = mid
+        b_lo, b_hi = blo.copy(), bhi.copy()
+        b_lo[np.arange(len(d)), d] = mid
+        lo = np.concatenate([lo[~bad], a_lo, b_lo])
+        hi = np.concatenate([hi[~bad], a_hi, b_hi])
+
+
+def adaptive_mesh(mol: Molecule, half_width: float, p: int, tol_m: float,
+                  uniform_levels: int = 3, max_level: int = 40) -> Mesh:
+    """Adaptive cell mesh per Section 3.2: uniform levels, then keep the 8
+    children of a cell whenever |int_C t - sum_i int_{C_i} t| >= tol_m with the
+    test function t = sqrt(rho0) * V_ext (Eq. test_function), then cut cells
+    through atoms and fix aspect ratios."""
+
+    def t_fn(pts):
+        return np.sqrt(density0(mol, pts)) * v_ext(mol, pts)
+
+    lo = np.full((1, 3), -half_width)
+    hi = np.full((1, 3), half_width)
+    for _ in range(uniform_levels):
+        lo, hi = _children(lo, hi)
+    final_lo, final_hi = [], []
+    front_lo, front_hi = lo, hi
+    front_int = _cell_integrals(t_fn, front_lo, front_hi, p)
+    level = uniform_levels
+    while front_lo.shape[0] and level < max_level:
+        clo, chi = _children(front_lo, front_hi)
+        cint = _cell_integrals(t_fn, clo, chi, p)
+        err = np.abs(front_int - cint.reshape(-1, 8).sum(axis=1))
+        refine = err >= tol_m
+        final_lo.append(front_lo[~refine])
+        final_hi.append(front_hi[~refine])
+        mask = np.repeat(refine, 8)
+        front_lo, front_hi, front_int = clo[mask], chi[mask], cint[mask]
+        level += 1
+    final_lo.append(front_lo)
+    final_hi.append(front_hi)
+    lo = np.concatenate(final_lo)
+    hi = np.concatenate(final_hi)
+    lo, hi = _split_at_atoms(lo, hi, mol.pos)
+    lo, hi = _fix_aspect(lo, hi)
+    # deterministic cell order (lexicographic by lower corner)
+    order = np.lexsort((lo[:, 2], lo[:, 1], lo[:, 0]))
+    return mesh_from_cells(lo[order], hi[order], p)
+
+
+# --------------------------------------------------------------------------
+# Workloads
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Workload:
+    """One Green-iteration input: mesh, effective potential, orbitals, density."""
+
+    name: str
+    mesh: Mesh
+    veff: np.ndarray  # (N,)
+    psi: np.ndarray  # (nw, N)
+    eps: np.ndarray  # (nw,) unshifted eigenvalue guesses
+    rho: np.ndarray  # (N,)
+    vshift: float
+    theta: float
+    degree: int
+    leaf_size: int
+    alpha: float = 1.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.mesh.n
+
+    @property
+    def k(self) -> np.ndarray:
+        """Yukawa decay rates k = sqrt(-2 (eps + V_shift)) (Eq. gauge-shift)."""
+        return np.sqrt(-2.0 * (self.eps + self.vshift))
+
+    @property
+    def f(self) -> np.ndarray:
+        """Convolution sources f = (V_eff + V_shift) psi, one row per orbital."""
+        return (self.veff + self.vshift)[None, :] * self.psi
+
+
+def hydrogen_1s(seed: int = 0, ncell: int = 8, p: int = 3, half_width: float = 10.0) -> Workload:
+    """Hydrogen 1s on a uniform [-10,10]^3 mesh of ncell^3 cells.
+
+    The nucleus sits on an interior cell vertex picked by the seed within
+    +-2.5 Bohr of the origin, so no quadrature node coincides with it.
+    psi = e^{-r}/sqrt(pi), V = -1/r, eps = -0.5, V_shift = 0, so k = 1.
+    """
+    mesh = uniform_mesh(-half_width, half_width, ncell, p)
+    h = 2 * half_width / ncell
+    rng = np.random.default_rng(seed)
+    cand = np.arange(-ncell // 2 + 1, ncell // 2) * h
+    cand = cand[np.abs(cand) <= 2.5 + 1e-12]
+    R = rng.choice(cand, size=3)
+    pts = mesh.xyz.T
+    r = _dist(pts, R)
+    psi = np.exp(-r) / math.sqrt(math.pi)
+    veff = -1.0 / r
+    rho = psi * psi
+    return Workload(name=f"H1s-{ncell}^3-p{p}", mesh=mesh, veff=veff, psi=psi[None, :],
+                    eps=np.array([-0.5]), rho=rho, vshift=0.0, theta=0.7, degree=6,
+                    leaf_size=2000, meta={"nucleus": R.tolist(), "seed": seed})
+
+
+def _smooth_perturbation(rng, pts, amp=0.01):
+    a = rng.normal(size=3)
+    a *= 0.5 / np.linalg.norm(a)
+    ph = rng.uniform(0, 2 * np.pi)
+    return 1.0 + amp * np.sin(pts @ a + ph)
+
+
+def lithium(seed: int = 1, tol_m: float = 3e-7, p: int = 4, half_width: float = 20.0,
+            uniform_levels: int = 3) -> Workload:
+    """Li atom at the origin: adaptive mesh on [-20,20]^3, p = 4, two occupied
+    orbitals (hydrogenic 1s and 2s with Z = 3, the 2s with a seeded 1% smooth
+    perturbation), V_eff = V_ext + V_H[rho0], Hartree source rho0.  The
+    default tolerance 3e-7 gives about 309k points (1e-5 gives 162k with this
+    test function)."""
+    mol = Molecule(["Li"], np.zeros((1, 3)))
+    mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
+    rng = np.random.default_rng(seed)
+    pts = mesh.xyz.T
+    r = _dist(pts, mol.pos[0])
+    psi1 = radial_orbital("1s", 3.0, r)
+    psi2 = radial_orbital("2s", 3.0, r) * _smooth_perturbation(rng, pts)
+    rho = density0(mol, pts)
+    veff = v_ext(mol, pts) + v_hartree0(mol, pts)
+    eps = np.array([-1.9, -0.11]) + rng.uniform(-0.02, 0.02, size=2)
+    return Workload(name="Li", mesh=mesh, veff=veff, psi=np.stack([psi1, psi2]), eps=eps,
+                    rho=rho, vshift=-0.5, theta=0.7, degree=8, leaf_size=2000,
+                    meta={"seed": seed, "tol_m": tol_m})
+
+
+def carbon_monoxide(seed: int = 2, tol_m: float = 3e-6, p: int = 4, half_width: float = 20.0,
+                    n_orb: int = 7, uniform_levels: int = 3) -> Workload:
+    """CO with C at (-1.06581,0,0) and O at (+1.06581,0,0) (Section 6):
+    adaptive mesh, n_orb orbitals from a seeded superposition of atomic
+    Slater orbitals, eps seeded uniformly in [-20, -0.3] Ha."""
+    mol = Molecule(["C", "O"], np.array([[-1.06581, 0.0, 0.0], [1.06581, 0.0, 0.0]]))
+    mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
+    return _molecule_workload("CO", mol, mesh, seed, n_orb)
+
+
+def benzene(seed: int = 3, tol_m: float = 3e-6, p: int = 4, half_width: float = 20.0,
+            n_orb: int = 21, uniform_levels: int = 3) -> Workload:
+    """C6H6 in the z=0 plane at the paper's geometry (Section 6)."""
+    C = [(-0.682781, 2.548170), (0.682781, -2.548170), (2.548230, -0.682767), (-2.548230, 0.682767),
+         (1.86544, 1.86541), (-1.86544, -1.86541)]
+    H = [(-1.21247, 4.52502), (1.21247, -4.52502), (4.52548, -1.21333), (-4.52548, 1.21333),
+         (3.31252, 3.31351), (-3.31252, -3.31351)]
+    pos = np.array([[x, y, 0.0] for x, y in C + H])
+    mol = Molecule(["C"] * 6 + ["H"] * 6, pos)
+    mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
+    return _molecule_workload("C6H6", mol, mesh, seed, n_orb)
+
+
+def _molecule_workload(name, mol, mesh, seed, n_orb):
+    rng = np.random.default_rng(seed)
+    pts = mesh.xyz.T
+    basis = []
+    for s, R in zip(mol.symbols, mol.pos):
+        r = _dist(pts, R)
+        for kind, _, Z in _shells(s):
+            basis.append(radial_orbital(kind, Z, r))
+            if kind == "2p":
+                for d in range(3):
+                    basis.append(radial_orbital("2p", Z, r) * (pts[:, d] - R[d]) / np.maximum(r, 1e-300))
+    basis = np.stack(basis)
+    coef = rng.normal(size=(n_orb, basis.shape[0]))
+    psi = coef @ basis
+    rho = density0(mol, pts)
+    veff = v_ext(mol, pts) + v_hartree0(mol, pts)
+    eps = np.sort(rng.uniform(-20.0, -0.3, size=n_orb))
+    return Workload(name=name, mesh=mesh, veff=veff, psi=psi, eps=eps, rho=rho, vshift=-0.5,
+                    theta=0.7, degree=8, leaf_size=2000, meta={"seed": seed, "n_orb": n_orb})
+
+
+def random_cube(n: int, seed: int = 0, half_width: float = 1.0):
+    """n uniformly random points in a cube with random positive weights and a
+    smooth field: the small parity stress case (ragged sizes, no mesh)."""
+    rng = np.random.default_rng(seed)
+    xyz = rng.uniform(-half_width, half_width, size=(3, n))
+    w = rng.uniform(0.5, 1.5, size=n) * (2 * half_width) ** 3 / max(n, 1)
+    return np.ascontiguousarray(xyz), w
