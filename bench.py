@@ -1,0 +1,400 @@
+"""Benchmark: one Green iteration of treecode-accelerated Green Iteration on GB300.
+
+A step is one pass of the whole hot path over one synthetic Li workload
+(hydrogenic Li, adaptive mesh of ~309k points, 2 occupied orbitals plus the
+Hartree sum, treecode degree 8, theta 0.7, leaf size 2000, FP32C):
+  tree + batches + interaction lists + work items   (tagi_tree_build)
+  field forming, anterpolation, near/far kernel,
+  SS epilogue, eigenvalue update, Gram-Schmidt,
+  normalisation, residuals, Hartree energy           (tagi_green_step)
+with inputs resident in HBM.  The metric is treecode interactions per second:
+one interaction = one (target, source-or-proxy, field) kernel evaluation,
+counted from the interaction lists.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank solves its own independent workload (seed = rank):
+weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "treecode kernel interactions/s at rel err 1e-6"
+UNIT = "interactions/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tagi", choices=["tagi", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain-form comparison step")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(seed):
+    from paper_2003_01833_gb300 import workloads as W
+
+    return W.lithium(seed=seed)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline model
+# Thread instructions issued per pair in the FP32C kernel, counted from the
+# source of tile_near / tile_far (FP32 pipe + MUFU; shared-memory loads and
+# loop overhead excluded).  Near: two-float coordinate difference 9, r^2 3,
+# rsqrt 1, r 1, r*w 1 -> 15 per pair; per Yukawa field k r 1, ex2 1, SS
+# difference 2, e*riw 1, accumulate 1 -> 6; Hartree 1 + 1 + 2 + 1 -> 5.
+# Far: difference 3, r^2 3, rsqrt 1, r 1 -> 8; per Yukawa field 1 + 1 + 1 + 1
+# + 1 -> 5; Hartree 1 + 1 + 1 + 1 + 1 -> 5.
+ISSUE_PER_SM_CLK = 128  # 4 schedulers x 32 lanes, one warp instruction each per clock
+
+
+def issue_per_pair(ny, hh):
+    near = 15 + 6 * ny + (5 if hh else 0)
+    far = 8 + 5 * ny + (5 if hh else 0)
+    return near, far
+
+
+def roofline(info, nfields_y, hh, kernel_ms, clk_mhz, sms):
+    near, far = issue_per_pair(nfields_y, hh)
+    nf = nfields_y + (1 if hh else 0)
+    instr = info["near_pairs"] * near + info["far_pairs"] * far
+    inter = (info["near_pairs"] + info["far_pairs"]) * nf
+    per_inter = instr / inter
+    peak = sms * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / per_inter  # interactions/s
+    achieved = inter / (kernel_ms * 1e-3)
+    return achieved, peak, per_inter
+
+
+# ------------------------------------------------------------------ oracle legs
+def cpu_oracle_rate(wl, budget_s=20.0, seed=0):
+    """Oracle (float64 CPU treecode, as it stands, OpenMP on every core) on a
+    bounded sample of the same workload: a seeded sample of target batches,
+    all three fields.  The oracle anterpolates every cluster on each call; that
+    cost is timed on its own (a call with no batch) and charged to the sample
+    in proportion to its share of the batches, as a full run would amortise it.
+    Returns interactions/s, threads used and a description of the sample."""
+    import oracle
+
+    m = wl.mesh
+    ot = oracle.Tree(m.xyz, wl.leaf_size)
+    b, c, k = ot.lists(wl.theta, wl.degree)
+    P = (wl.degree + 1) ** 3
+    size = ot.end - ot.begin
+    per_batch = {}
+    for bb, cc, kk in zip(b, c, k):
+        per_batch[bb] = per_batch.get(bb, 0) + (P if kk == 1 else int(size[cc]))
+    leaves = np.array(ot.leaves)
+    rng = np.random.default_rng(seed)
+    rng.shuffle(leaves)
+    fields = [(0, wl.k[o], wl.f[o]) for o in range(wl.psi.shape[0])] + [(1, wl.alpha, wl.rho)]
+    nf = len(fields)
+    t_ant = 0.0
+    for kern, par, f in fields:
+        ts = time.time()
+        ot.treecode_batches(wl.theta, wl.degree, kern, par, f, m.w, [])
+        t_ant += time.time() - ts
+    # size the sample from one probe batch
+    ts = time.time()
+    kern, par, f = fields[0]
+    ot.treecode_batches(wl.theta, wl.degree, kern, par, f, m.w, leaves[:1])
+    t_probe = max(time.time() - ts - t_ant / nf, 1e-3)
+    nb = int(max(1, min(len(leaves), (budget_s - 2 * t_ant) / (nf * t_probe))))
+    pick = leaves[:nb]
+    t_b = 0.0
+    for kern, par, f in fields:
+        ts = time.time()
+        ot.treecode_batches(wl.theta, wl.degree, kern, par, f, m.w, pick)
+        t_b += time.time() - ts
+    t_b -= t_ant
+    inter = sum(per_batch[x] * int(size[x]) for x in pick) * nf
+    share = nb / len(leaves)
+    threads = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    desc = (f"{nb} of {len(leaves)} target batches x {nf} fields of this workload: {t_b:.2f} s of batch work + "
+            f"{share:.3f} x {t_ant:.2f} s whole-tree anterpolation")
+    return inter / (t_b + share * t_ant), threads, desc, t_b + t_ant
+
+
+def run_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return
+    wl = make_workload(0)
+    rates = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        rate, threads, desc, _ = cpu_oracle_rate(wl, budget_s=8.0, seed=i)
+        if i >= args.warmup:
+            rates.append(rate)
+    v = float(np.mean(rates))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"Li atom, {wl.n} mesh points, 2 orbitals + Hartree, degree 8, theta 0.7, "
+                                  "leaf 2000", "model": "oracle treecode (float64 CPU)"},
+           "cpu_baseline": {"kind": "oracle", "value": v, "unit": UNIT, "cores": threads, "sample": desc},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import paper_2003_01833_gb300.tagi as T
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    T.lib()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    wl = make_workload(seed=1 + rank)
+    n = wl.n
+    nw = wl.psi.shape[0]
+    xyz = torch.tensor(wl.mesh.xyz, device=dev)
+    w = torch.tensor(wl.mesh.w, device=dev)
+    veff = torch.tensor(wl.veff, device=dev)
+    rho = torch.tensor(wl.rho, device=dev)
+    psi0 = torch.tensor(wl.psi, device=dev)
+    psi = psi0.clone()
+    vh = torch.empty(n, dtype=torch.float64, device=dev)
+    params = T.make_params(theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size, prec=T.TAGI_FP32C)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step(psi_buf):
+        h = T.tagi_tree_build(xyz, w, params)
+        psi_buf.copy_(psi0)
+        eps, res, eh = T.tagi_green_step(h, veff, wl.vshift, psi_buf, wl.eps, rho=rho, vh=vh)
+        return h, eps, res, eh
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        h, *_ = step(psi)
+        T.tagi_tree_destroy(h)
+    torch.cuda.synchronize()
+
+    # ---- timed steps (device resident inputs), L2 flushed before each step
+    T.tagi_profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    times = []
+    info = None
+    launches0 = T.tagi_kernel_launches()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h, eps, res, eh = step(psi)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        if info is None:
+            info = T.tagi_tree_info(h)
+        T.tagi_tree_destroy(h)
+    launches = (T.tagi_kernel_launches() - launches0 - 0) / args.steps
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = {g: T.tagi_profile_read(g) for g in T.PROFILE_GROUPS}
+    T.tagi_profile_enable(False)
+    ms = float(np.mean(times))
+    nf = nw + 1
+    inter = (info["near_pairs"] + info["far_pairs"]) * nf
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+        tot = torch.tensor([float(inter)], device=dev)
+        torch.distributed.all_reduce(tot)
+        inter_all = float(tot.item())
+    else:
+        inter_all = float(inter)
+    value = inter_all / (t_max * 1e-3)
+
+    # ---- end to end through the public API: pinned host inputs -> device,
+    # step, results -> host, all inside the timed region
+    hx = torch.tensor(wl.mesh.xyz).pin_memory()
+    hw = torch.tensor(wl.mesh.w).pin_memory()
+    hv = torch.tensor(wl.veff).pin_memory()
+    hr = torch.tensor(wl.rho).pin_memory()
+    hp = torch.tensor(wl.psi).pin_memory()
+    out_psi = torch.empty_like(hp).pin_memory()
+    out_vh = torch.empty(n, dtype=torch.float64).pin_memory()
+    dx, dw, dv, dr, dp = (torch.empty_like(a, device=dev) for a in (hx, hw, hv, hr, hp))
+    dvh = torch.empty(n, dtype=torch.float64, device=dev)
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d_, h_ in ((dx, hx), (dw, hw), (dv, hv), (dr, hr), (dp, hp)):
+            d_.copy_(h_, non_blocking=True)
+        hh = T.tagi_tree_build(dx, dw, params)
+        T.tagi_green_step(hh, dv, wl.vshift, dp, wl.eps, rho=dr, vh=dvh)
+        out_psi.copy_(dp, non_blocking=True)
+        out_vh.copy_(dvh, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+        T.tagi_tree_destroy(hh)
+    e2e_s = float(np.mean(e2e_times))
+    h2d = 8 * n * (3 + 1 + 1 + 1 + nw)
+    d2h = 8 * n * (nw + 1)
+
+    # ---- plain FP64 form: one orbital per launch, same tree, no graph
+    plain = None
+    if not args.no_plain and rank == 0:
+        pp = T.make_params(theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size, prec=T.TAGI_FP64)
+        psi64 = psi0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h64 = T.tagi_tree_build(xyz, w, pp)
+        eps64, res64, eh64 = T.tagi_green_step(h64, veff, wl.vshift, psi64, wl.eps, rho=rho, vh=vh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        T.tagi_tree_destroy(h64)
+        plain_ms = e0.elapsed_time(e1)
+        # accuracy of the FP32C step against the FP64 plain form on the GPU
+        psi32 = psi0.clone()
+        h = T.tagi_tree_build(xyz, w, params)
+        eps32, res32, eh32 = T.tagi_green_step(h, veff, wl.vshift, psi32, wl.eps, rho=rho, vh=vh)
+        T.tagi_tree_destroy(h)
+        a, b = psi32.cpu().numpy(), psi64.cpu().numpy()
+        rel = [float(np.linalg.norm(a[o] - b[o]) / np.linalg.norm(b[o])) for o in range(nw)]
+        plain = {"s_per_green_iteration_fp64_plain": plain_ms * 1e-3, "speedup_vs_plain": plain_ms / ms,
+                 "fp32c_vs_fp64_psi_rel_l2": rel, "fp32c_vs_fp64_eps_abs": [float(x) for x in np.abs(eps32 - eps64)],
+                 "fp32c_vs_fp64_eh_abs": abs(eh32 - eh64)}
+
+    if rank != 0:
+        return
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    k_ms, k_cnt = prof["interact"]
+    k_ms_per_step = k_ms / max(1, args.steps)
+    clk_mhz = clk.get("sm_mhz") or 1900.0
+    achieved, peak, per_inter = roofline(info, nw, True, k_ms_per_step, clk_mhz, sms)
+    cpu = None
+    if not args.no_cpu:
+        rate, threads, desc, _ = cpu_oracle_rate(wl, budget_s=20.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
+        "config": {"workload": f"Li atom (hydrogenic Z=3, adaptive mesh p=4, tol_m 3e-7): {n} points, "
+                               f"{nw} orbitals + Hartree, degree {wl.degree}, theta {wl.theta}, leaf {wl.leaf_size}",
+                   "step": "tree+lists+items, fields, anterpolation, near/far kernel, SS epilogue, "
+                           "eps update, MGS, residuals, E_H",
+                   "interactions_per_step": inter, "near_pairs": info["near_pairs"], "far_pairs": info["far_pairs"],
+                   "l2": "flushed (256 MB write) before each timed step", "parallelism": f"replicas x{world}"},
+        "s_per_green_iteration": t_max * 1e-3,
+        "phases_ms_per_step": {g: prof[g][0] / max(1, args.steps) for g in prof},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "interactions/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_interact32 (near/far)", "issue_per_interaction": per_inter,
+                     "peak_model": f"{sms} SMs x 128 issue/clk x {clk_mhz:.0f} MHz / {per_inter:.2f} instr per "
+                                   "interaction (measured clock)"},
+        "clocks": clk,
+        "e2e": {"value": inter_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "s_per_step": e2e_s},
+        "gpu_launches": launches,
+        "plain_fp64": plain,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * tagi.h -- C ABI of the treecode-accelerated Green Iteration hot path
+ * (arXiv:2003.01833): the discrete convolution sums of Green Iteration with
+ * the modified-Helmholtz (Yukawa) kernel and the Coulomb kernel, both with
+ * singularity subtraction, evaluated by a barycentric Lagrange treecode.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers marked [dev] are CUDA device pointers, [host] are host
+ *     pointers.  The caller owns every buffer it passes; the library never
+ *     frees or keeps them, except that tagi_tree_build copies xyz and w.
+ *   - Point arrays are in the caller's order.  Coordinates are structure of
+ *     arrays: xyz[0..n) = x, xyz[n..2n) = y, xyz[2n..3n) = z, all float64.
+ *     Field arrays are row-major (nf, n) float64.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  Entry points that return host values
+ *     (tagi_green_step, tagi_tree_info) synchronise the stream.
+ *   - No exception crosses the ABI.  Every call returns a tagi_status; on
+ *     failure tagi_last_error() gives a message (thread-local, valid until
+ *     the next call on the same thread).
+ *   - Kernel convention: G_k(r) = exp(-k r) / (4 pi r), so the paper's
+ *     Green's function (Eq. Hemlholtz_Greens_Function) is -2 G_k with
+ *     k = sqrt(-2 eps); G_C(r) = 1 / r (Eq. Coulomb).
+ */
+#ifndef TAGI_H
+#define TAGI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TAGI_OK = 0,
+    TAGI_ERR_INVALID_ARG = 1, /* a size, parameter or input value is out of range */
+    TAGI_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+    TAGI_ERR_OOM = 3,         /* device or host allocation failed */
+    TAGI_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    TAGI_ERR_STATE = 5        /* the object is not in a state that allows the call */
+} tagi_status;
+
+typedef enum {
+    TAGI_FP64 = 0,  /* plain form: every sum and every kernel value in float64 */
+    TAGI_FP32C = 1  /* float32 kernel sums, per-target two-float (compensated)
+                       accumulation, float64 singularity-subtraction epilogue */
+} tagi_precision;
+
+/* Treecode parameters (Section 5; Eq. MAC; Algorithm 3).
+ *   theta      MAC parameter, 0 <= theta < 1.  theta = 0 never approximates,
+ *              so the treecode reduces to the direct sum of Eq. direct-sum.
+ *   degree     interpolation degree n, 1 <= n <= 9; (n+1)^3 proxies per cluster.
+ *   leaf_size  maximum leaf size N_L >= 1.
+ *   batch_size maximum batch size N_B; must equal leaf_size (the batches are
+ *              the leaves, Section 5.1) or be 0 (taken as leaf_size).
+ *   prec       TAGI_FP64 or TAGI_FP32C.
+ *   ss         1: singularity subtraction (Eq. yukawa-conv-ss, coulomb-conv-ss); 0: none.
+ *   alpha      Gaussian width of the Coulomb subtraction (Eq. coulomb-conv-ss), > 0. */
+typedef struct {
+    double theta;
+    int degree;
+    int leaf_size;
+    int batch_size;
+    int prec;
+    int ss;
+    double alpha;
+} tagi_params;
+
+typedef struct tagi_tree tagi_tree; /* opaque, owned by the library */
+
+/* Sizes of a built tree (host struct filled by tagi_tree_info). */
+typedef struct {
+    int64_t n_points;
+    int32_t n_clusters;
+    int32_t n_leaves;       /* = number of target batches */
+    int32_t depth;          /* number of levels below the root */
+    int32_t n_far_clusters; /* clusters approximated by at least one batch */
+    int64_t n_list_entries; /* batch-cluster entries after near-field leaf expansion */
+    int64_t n_items;        /* work items of the near/far kernel */
+    int64_t near_pairs;     /* sum over batches |B| * (sources in near entries) */
+    int64_t far_pairs;      /* sum over batches |B| * (proxies in far entries) */
+    int32_t degree;         /* interpolation degree n */
+    int32_t n_proxies;      /* (n+1)^3 proxies per cluster */
+} tagi_tree_stats;
+
+/* Build the source-cluster tree and target batches (Algorithm 3 line 1,
+ * Section 5.1), the per-batch interaction lists of Algorithm 3's
+ * ComputePotential under the MAC of Eq. MAC, the proxy grid of every cluster
+ * that some batch approximates (Chebyshev points of the second kind,
+ * Section 5.2) and the anterpolated quadrature weights w^ of those clusters.
+ *   xyz [dev] 3*n float64, w [dev] n float64 (quadrature weights, finite).
+ *   n >= 1.  params [host].  out [host] receives the new tree.
+ * Tree rules where the paper is silent: root = minimal bounding box; a
+ * cluster is a leaf iff it holds <= leaf_size points; the dimensions split
+ * are those whose extent e satisfies e*sqrt(2) >= the largest extent; the cut
+ * is at (lo+hi)*0.5 of the shrunk box, a point with x >= mid goes up; empty
+ * children are dropped.  Errors: TAGI_ERR_INVALID_ARG for n < 1, bad params,
+ * non-finite xyz or w, or a tree deeper than 64 levels. */
+tagi_status tagi_tree_build(const double* xyz, const double* w, int64_t n, const tagi_params* params,
+                            void* stream, tagi_tree** out);
+
+/* Free the tree and every device buffer it owns.  NULL is accepted. */
+tagi_status tagi_tree_destroy(tagi_tree* tree);
+
+/* Fill *stats [host] (synchronises the stream used at build). */
+tagi_status tagi_tree_info(const tagi_tree* tree, tagi_tree_stats* stats);
+
+/* Copy the tree's integer structure and boxes out for inspection.
+ *   perm [host] n int32: tree position -> caller index.
+ *   begin, end [host] n_clusters int32 each: the cluster owns positions [begin, end).
+ *   lo, hi [host] 3*n_clusters float64 (x, y, z per cluster).
+ *   parent, nchild [host] n_clusters int32; child [host] 8*n_clusters int32.
+ *   Any pointer may be NULL to skip that array. */
+tagi_status tagi_tree_export(const tagi_tree* tree, int32_t* perm, int32_t* begin, int32_t* end,
+                             double* lo, double* hi, int32_t* parent, int32_t* nchild,
+                             int32_t* child);
+
+/* Copy the interaction lists out: for every list entry (in batch order)
+ * batch cluster id, source cluster id and kind (0 = direct sum, Eq.
+ * direct-sum_2; 1 = approximation, Eq. particle-cluster-approx-rearranged).
+ * Direct entries are expanded to the leaves under the cluster Algorithm 3
+ * named.  cap: capacity of each host array; *count receives the total. */
+tagi_status tagi_tree_lists(const tagi_tree* tree, int64_t cap, int32_t* batch, int32_t* cluster,
+                            int32_t* kind, int64_t* count);
+
+/* Proxy weights of Eq. particle-cluster-approx-rearranged,
+ *   qh[c][j][k] = sum_{i in cluster c} L_k1(x_i) L_k2(y_i) L_k3(z_i) q[j][i],
+ * for EVERY cluster c of the tree (not only the approximated ones), with the
+ * barycentric basis of Eq. Lagrange_polynomials / barycentric_weights on the
+ * cluster's Chebyshev points of the second kind.
+ *   q [dev] nq*n float64 charges in the caller's order; nq >= 1.
+ *   qh [dev] n_clusters*nq*(degree+1)^3 float64, caller-owned.
+ * Computed in float64 whatever the tree's precision. */
+tagi_status tagi_anterpolate(tagi_tree* tree, const double* q, int nq, double* qh, void* stream);
+
+/* Yukawa convolution for nf fields with their own decay rates:
+ *   u[o][i] = sum_{j, r_ij != 0} G_{k_o}(r_ij) (f[o][j] - f[o][i]) w_j + f[o][i] / k_o^2   (ss = 1)
+ *   u[o][i] = sum_{j, r_ij != 0} G_{k_o}(r_ij) f[o][j] w_j                                (ss = 0)
+ * evaluated by the treecode (Eq. direct-sum, yukawa-conv-ss, Algorithm 3).
+ *   f [dev] nf*n float64; k [host] nf float64, each finite and > 0;
+ *   u [dev] nf*n float64, caller-owned.  nf >= 1. */
+tagi_status tagi_yukawa_conv(tagi_tree* tree, const double* f, const double* k, int nf, double* u,
+                             void* stream);
+
+/* Coulomb (Hartree) convolution by the treecode (Eq. Coulomb, coulomb-conv-ss):
+ *   vh[i] = sum_{j, r != 0} (rho_j - rho_i exp(-r^2/alpha^2)) w_j / r + 2 pi alpha^2 rho_i  (ss = 1)
+ *   vh[i] = sum_{j, r != 0} rho_j w_j / r                                                  (ss = 0)
+ *   rho [dev] n float64; vh [dev] n float64, caller-owned. */
+tagi_status tagi_coulomb_conv(tagi_tree* tree, const double* rho, double* vh, void* stream);
+
+/* One Green iteration for nw orbitals at once (Algorithm 2 lines 3-6):
+ *   f_o = (veff + vshift) psi_o, k_o = sqrt(-2 (eps_o + vshift))  (Eq. gauge-shift)
+ *   psi~_o = -2 * Yukawa_{k_o}[f_o]                               (Eq. Yukawa)
+ *   eps'_o <- eps'_o - <f_o, psi_o - psi~_o> / <psi~_o, psi~_o>   (Eq. gradient-free, shifted eps' = eps + vshift)
+ *   modified Gram-Schmidt of psi~ in index order, then normalisation,
+ * with every inner product weighted by the quadrature, <a, b> = sum a_i b_i w_i.
+ * With rho non-NULL the Hartree potential is computed in the same pass
+ * (tagi_coulomb_conv's formula) into vh, and E_H = 1/2 sum vh rho w
+ * (Eq. quadrature-example) into *eh.
+ *   veff [dev] n; psi [dev] nw*n, in: current orbitals, out: new orbitals;
+ *   eps [host] nw, in: current unshifted eigenvalues, out: updated ones;
+ *   rho [dev] n or NULL; vh [dev] n or NULL (required when rho is given);
+ *   resid [host] nw or NULL: ||psi_new - psi_old||_w; eh [host] or NULL.
+ * Errors: TAGI_ERR_INVALID_ARG when eps_o + vshift >= 0 (no decay, Section 3.3).
+ * Synchronises the stream. */
+tagi_status tagi_green_step(tagi_tree* tree, const double* veff, double vshift, double* psi,
+                            double* eps, int nw, const double* rho, double* vh, double* resid,
+                            double* eh, void* stream);
+
+/* Diagnostics (no counterpart in the paper).
+ * tagi_kernel_launches: number of CUDA kernels this library has launched in
+ * this process so far (monotonic; differences bracket a region of interest).
+ * tagi_profile_enable: on != 0 starts CUDA-event timing of the phases of
+ * every call (and clears earlier totals); 0 stops it.  Timing adds two event
+ * records per phase on the call's stream.
+ * tagi_profile_read: total milliseconds and number of timed phases so far for
+ * one group: 0 = tree, lists and items (tagi_tree_build), 1 = field
+ * preparation and anterpolation, 2 = near/far interaction kernel(s),
+ * 3 = SS epilogue, 4 = Green-step reductions.  Synchronises the recorded
+ * events.  ms, count [host], either may be NULL. */
+int64_t tagi_kernel_launches(void);
+
+/* Mean relative bias of the float32 kernel values of the TAGI_FP32C path on
+ * the current device, weighted as in the singularity-subtraction integrals:
+ * *beta_yukawa for exp(-k r)/r (weight r e^{-k r}), *beta_gauss for
+ * exp(-r^2/alpha^2)/r (weight r e^{-r^2/alpha^2}).  Measured once per device
+ * and process by a deterministic kernel (first FP32C call); the SS epilogue
+ * scales the analytic terms f/k^2 and 2 pi alpha^2 rho by (1 + beta) so the
+ * subtraction cancels against the float32 sums.  Outputs [host], may be NULL. */
+tagi_status tagi_fp32_bias(double* beta_yukawa, double* beta_gauss, void* stream);
+tagi_status tagi_profile_enable(int on);
+tagi_status tagi_profile_read(int group, double* ms, int64_t* count);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* tagi_last_error(void);
+
+/* Library version string. */
+const char* tagi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TAGI_H */

@@ -1,0 +1,305 @@
+// Field preparation, the singularity-subtraction epilogue and the float64
+// reductions of the Green step (Algorithm 2 lines 3-6, Eq. gradient-free,
+// Eq. quadrature-example).
+//
+// All reductions are two-stage with a fixed grid and a fixed summation order,
+// so results are bitwise reproducible run to run.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "tagi_internal.cuh"
+
+namespace tagi {
+
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 608;  // 4 per SM on a 152-SM GB300
+constexpr double kPi = 3.14159265358979323846;
+
+inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+// Two-float split of each field value, f = fh + fl, and the rounded charge
+// f w for the anterpolation.
+__global__ void k_prepare32(const double* __restrict__ f, int nf, int64_t n, const int* __restrict__ perm,
+                            const double* __restrict__ pw, float* fa, int64_t lda, float* fb, float* qa)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nf) return;
+    int64_t o = i / n, p = i % n;
+    double v = f[o * n + perm[p]];
+    float h = (float)v;
+    fa[o * lda + p] = h;
+    fb[o * n + p] = (float)(v - (double)h);
+    qa[o * n + p] = (float)(v * pw[p]);
+}
+
+__global__ void k_prepare64(const double* __restrict__ f, int nf, int64_t n, const int* __restrict__ perm,
+                            const double* __restrict__ pw, double* q, int64_t ldq, double* c)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nf) return;
+    int64_t o = i / n, p = i % n;
+    double v = f[o * n + perm[p]];
+    q[o * ldq + p] = v * pw[p];
+    c[o * n + p] = v;
+}
+
+struct EpiField {
+    double* out;
+    double kval;  // k (Yukawa, the value the interaction kernel applied) or alpha (Coulomb)
+    double cfac;  // factor on the analytic SS term: 1 + the kernel's measured mean bias
+    int kind;
+    int pad;
+};
+constexpr int kEpiMax = 32;
+struct EpiFields {
+    EpiField f[kEpiMax];
+};
+
+// One CTA per target chunk: sum the chunk's item partials in item order, add
+// the SS constant and the kernel normalisation, scatter to the caller's order.
+__global__ void k_epilogue(EpiFields E, int nf_g, int field0, int nf_tot, const int* __restrict__ tc_item0,
+                           const int* __restrict__ tc_t0, const int* __restrict__ tc_t1, const int* __restrict__ perm,
+                           const double* __restrict__ part, const float* __restrict__ c32, int64_t ldc32,
+                           const double* __restrict__ c64, int64_t n, int ss)
+{
+    const int tc = blockIdx.x;
+    const int t = tc_t0[tc] + threadIdx.x;
+    if (t >= tc_t1[tc]) return;
+    const int i0 = tc_item0[tc], i1 = tc_item0[tc + 1];
+    const int dest = perm[t];
+    for (int g = 0; g < nf_g; g++) {
+        const int o = field0 + g;
+        double S = 0.0;
+        for (int it = i0; it < i1; it++) S += part[((size_t)it * nf_tot + o) * kTargetsPerItem + threadIdx.x];
+        const double c = c32 ? (double)c32[(size_t)o * ldc32 + t] : c64[(size_t)o * n + t];
+        const EpiField F = E.f[g];
+        double u;
+        if (F.kind == 0)  // G_k = e^{-kr}/(4 pi r); SS constant 4 pi c / k^2 over 4 pi
+            u = S / (4.0 * kPi) + (ss ? F.cfac * c / (F.kval * F.kval) : 0.0);
+        else  // Coulomb; SS constant 2 pi alpha^2 c (Eq. correction_term)
+            u = S + (ss ? F.cfac * 2.0 * kPi * F.kval * F.kval * c : 0.0);
+        F.out[dest] = u;
+    }
+}
+
+// ---------------------------------------------------------------- dots
+struct DotJob {
+    const double *x, *zx, *y, *zy;
+};
+constexpr int kDotMax = 16;
+struct DotJobs {
+    DotJob j[kDotMax];
+};
+
+// D_j = sum_i (x_j - zx_j)_i (y_j - zy_j)_i w_i ; zx / zy may be null.
+__global__ void k_dot1(DotJobs J, int nj, const double* __restrict__ w, int64_t n, double* part)
+{
+    __shared__ double sm[kRedThreads];
+    for (int j = 0; j < nj; j++) {
+        const DotJob d = J.j[j];
+        double s = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
+            double a = d.x[i] - (d.zx ? d.zx[i] : 0.0);
+            double b = d.y[i] - (d.zy ? d.zy[i] : 0.0);
+            s += a * b * w[i];
+        }
+        sm[threadIdx.x] = s;
+        __syncthreads();
+        for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+            if (threadIdx.x < off) sm[threadIdx.x] += sm[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(size_t)j * gridDim.x + blockIdx.x] = sm[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_dot2(const double* part, int nblk, double* out)
+{
+    __shared__ double sm[kRedThreads];
+    const int j = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += kRedThreads) s += part[(size_t)j * nblk + b];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) sm[threadIdx.x] += sm[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = sm[0];
+}
+
+__global__ void k_form(const double* __restrict__ veff, double vshift, const double* __restrict__ psi, int nw,
+                       int64_t n, double* f)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n * nw) f[i] = (veff[i % n] + vshift) * psi[i];
+}
+
+__global__ void k_scale(double* a, int64_t n, double s)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] *= s;
+}
+
+// y -= d[0] * x
+__global__ void k_axpy_dev(const double* __restrict__ x, double* y, int64_t n, const double* d)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] -= d[0] * x[i];
+}
+
+// y /= sqrt(d[0])
+__global__ void k_normalize(double* y, int64_t n, const double* d)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] /= sqrt(d[0]);
+}
+
+// eps'_o -= a_o / b_o (Eq. gradient-free); a, b interleaved in dots[2 o], dots[2 o + 1]
+__global__ void k_eps_update(double* eps, const double* dots, int nw)
+{
+    int o = threadIdx.x + blockIdx.x * blockDim.x;
+    if (o < nw) eps[o] -= dots[2 * o] / dots[2 * o + 1];
+}
+
+__global__ void k_sqrt(double* a, int n)
+{
+    int i = threadIdx.x + blockIdx.x * blockDim.x;
+    if (i < n) a[i] = sqrt(a[i]);
+}
+
+void run_dots(Tree& T, const std::vector<DotJob>& jobs, double* out_dev)
+{
+    cudaStream_t s = T.stream;
+    T.scratch.ensure(sizeof(double) * kDotMax * kRedBlocks);
+    for (size_t j0 = 0; j0 < jobs.size(); j0 += kDotMax) {
+        DotJobs J{};
+        int nj = (int)std::min<size_t>(kDotMax, jobs.size() - j0);
+        for (int j = 0; j < nj; j++) J.j[j] = jobs[j0 + j];
+        launch(k_dot1, kRedBlocks, kRedThreads, 0, s, J, nj, T.wc.as<double>(), T.n, T.scratch.as<double>());
+        launch(k_dot2, nj, kRedThreads, 0, s, T.scratch.as<double>(), kRedBlocks, out_dev + j0);
+        TAGI_LAUNCH_CHECK();
+    }
+}
+
+}  // namespace
+
+void prepare_points32(Tree& T, const double* f, int nf)
+{
+    T.fa.ensure(sizeof(float) * (size_t)nf * T.nrec);
+    T.fb.ensure(sizeof(float) * (size_t)nf * T.n);
+    T.qant.ensure(sizeof(float) * (size_t)nf * T.n);
+    launch(k_prepare32, nblocks(T.n * nf, 256), 256, 0, T.stream, f, nf, T.n, T.perm.as<int>(), T.pw.as<double>(),
+                                                             T.fa.as<float>(), T.nrec, T.fb.as<float>(),
+                                                             T.qant.as<float>());
+    TAGI_LAUNCH_CHECK();
+}
+
+void prepare_points64(Tree& T, const double* f, int nf)
+{
+    T.q64.ensure(sizeof(double) * (size_t)nf * T.nrec);
+    T.c64.ensure(sizeof(double) * (size_t)nf * T.n);
+    launch(k_prepare64, nblocks(T.n * nf, 256), 256, 0, T.stream, f, nf, T.n, T.perm.as<int>(), T.pw.as<double>(),
+                                                             T.q64.as<double>(), T.nrec, T.c64.as<double>());
+    TAGI_LAUNCH_CHECK();
+}
+
+void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* kval, const double* part, double* const* out)
+{
+    const bool fp32 = T.prec == TAGI_FP32C;
+    // FP32C: the subtracted sum c_i sum_j G~ w_j carries the mean bias beta of
+    // the float32 kernel values, and cancels against the analytic SS term; the
+    // analytic term gets the same factor (1 + beta) and the Yukawa decay rate
+    // the kernel applied, so the subtraction telescopes.
+    double by = 0.0, bg = 0.0;
+    if (fp32) fp32_bias(T.stream, &by, &bg);
+    for (int g0 = 0; g0 < nf; g0 += kEpiMax) {
+        int g = std::min(kEpiMax, nf - g0);
+        EpiFields E{};
+        for (int u = 0; u < g; u++) {
+            const int kind = kinds[g0 + u];
+            double kv = kval[g0 + u], cf = 1.0;
+            if (fp32) {
+                kv = kind == 0 ? effective_k32(kv) : effective_alpha32(kv);
+                cf = 1.0 + (kind == 0 ? by : bg);
+            }
+            E.f[u] = EpiField{out[g0 + u], kv, cf, kind, 0};
+        }
+        launch(k_epilogue, (int)T.ntchunk, kTargetsPerItem, 0, T.stream, 
+            E, g, g0, nf, T.tc_item0.as<int>(), T.tc_t0.as<int>(), T.tc_t1.as<int>(), T.perm.as<int>(), part,
+            fp32 ? T.fa.as<float>() : nullptr, T.nrec, fp32 ? nullptr : T.c64.as<double>(), T.n, T.ss);
+        TAGI_LAUNCH_CHECK();
+    }
+}
+
+void form_fields(Tree& T, const double* veff, double vshift, const double* psi, int nw, double* f)
+{
+    launch(k_form, nblocks(T.n * nw, 256), 256, 0, T.stream, veff, vshift, psi, nw, T.n, f);
+    TAGI_LAUNCH_CHECK();
+}
+
+void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, double* eps_s, double* resid)
+{
+    cudaStream_t s = T.stream;
+    const int64_t n = T.n;
+    const int nb = nblocks(n, 256);
+    // psi~ = -2 u (Eq. Yukawa)
+    launch(k_scale, nblocks(n * nw, 256), 256, 0, s, u, n * nw, -2.0);
+    TAGI_LAUNCH_CHECK();
+    DevBuf dd;
+    dd.ensure(sizeof(double) * (3 * (size_t)nw + 8));
+    double* dots = dd.as<double>();          // 2 nw
+    double* epsd = dots + 2 * nw;            // nw
+    double* one = epsd + nw;                 // scalars
+    // gradient-free update uses psi~ before orthogonalisation
+    std::vector<DotJob> jobs;
+    for (int o = 0; o < nw; o++) {
+        jobs.push_back(DotJob{f + o * n, nullptr, psi + o * n, u + o * n});
+        jobs.push_back(DotJob{u + o * n, nullptr, u + o * n, nullptr});
+    }
+    run_dots(T, jobs, dots);
+    TAGI_CUDA(cudaMemcpyAsync(epsd, eps_s, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
+    launch(k_eps_update, 1, 64 * ((nw + 63) / 64), 0, s, epsd, dots, nw);
+    TAGI_LAUNCH_CHECK();
+    // modified Gram-Schmidt in index order under <a, b>_w
+    for (int o = 0; o < nw; o++) {
+        double* v = u + o * n;
+        for (int p = 0; p < o; p++) {
+            run_dots(T, {DotJob{v, nullptr, u + p * n, nullptr}}, one);
+            launch(k_axpy_dev, nb, 256, 0, s, u + p * n, v, n, one);
+        }
+        run_dots(T, {DotJob{v, nullptr, v, nullptr}}, one);
+        launch(k_normalize, nb, 256, 0, s, v, n, one);
+        TAGI_LAUNCH_CHECK();
+    }
+    // residual ||psi_new - psi_old||_w, then psi <- psi_new
+    jobs.clear();
+    for (int o = 0; o < nw; o++) jobs.push_back(DotJob{u + o * n, psi + o * n, u + o * n, psi + o * n});
+    run_dots(T, jobs, dots);
+    launch(k_sqrt, 1, 64 * ((nw + 63) / 64), 0, s, dots, nw);
+    TAGI_CUDA(cudaMemcpyAsync(psi, u, sizeof(double) * n * nw, cudaMemcpyDeviceToDevice, s));
+    TAGI_CUDA(cudaMemcpyAsync(eps_s, epsd, sizeof(double) * nw, cudaMemcpyDeviceToHost, s));
+    std::vector<double> r(nw);
+    TAGI_CUDA(cudaMemcpyAsync(r.data(), dots, sizeof(double) * nw, cudaMemcpyDeviceToHost, s));
+    TAGI_CUDA(cudaStreamSynchronize(s));
+    if (resid)
+        for (int o = 0; o < nw; o++) resid[o] = r[o];
+}
+
+double weighted_dot(Tree& T, const double* a, const double* b)
+{
+    DevBuf d;
+    d.ensure(64);
+    run_dots(T, {DotJob{a, nullptr, b, nullptr}}, d.as<double>());
+    double h = 0;
+    TAGI_CUDA(cudaMemcpyAsync(&h, d.p, sizeof(double), cudaMemcpyDeviceToHost, T.stream));
+    TAGI_CUDA(cudaStreamSynchronize(T.stream));
+    return h;
+}
+
+}  // namespace tagi

@@ -1,0 +1,570 @@
+// Batch-cluster interactions: the near field (Eq. direct-sum_2, r = 0 skipped)
+// and the far field (Eq. particle-cluster-approx-rearranged) in one kernel.
+//
+// Both have the same direct-sum structure, so the kernel sees only "source
+// records": mesh points for direct entries and proxy points for approximated
+// ones.  A record carries a position, a weight omega and one charge q per
+// field: omega = w_j, q = f_j w_j for points; omega = w^_k, q = q^_k for
+// proxies.  With the singularity subtraction of Section 3.3 (far-field form
+// reading: two anterpolated charge sets) every field accumulates
+//   Yukawa:   sum_s exp(-k r) / r * (q_s - c_i omega_s)
+//   Coulomb:  sum_s (q_s - c_i omega_s exp(-r^2 / alpha^2)) / r
+// where c_i = f(x_i); the constant terms c_i/k^2 and 2 pi alpha^2 c_i and the
+// 1/(4 pi) of G_k are added by the epilogue.
+//
+// FP32C kernel: all fields of a call (each Yukawa field with its own k, plus
+// the Hartree field) share one pass over the geometry.  Each CTA owns up to
+// 256 targets of one batch (128 threads x 2 targets) and a contiguous segment
+// of the batch's interaction list; source tiles of 256 records are staged in
+// shared memory with positions shifted from the record's frame (its leaf or
+// cluster center) to the batch center.  Near-field records are two-float
+// (position and field value, see tile_near); proxies are single float.
+// rsqrt and exp2 use the MUFU unit (rsqrt.approx, ex2.approx); their mean
+// bias is measured once per device (fp32_bias) and compensated in the SS
+// epilogue.  Quadrature weights of mesh points are two-float too: adaptive
+// octree cells scale by powers of two, so a float32 rounding of w repeats the
+// same few relative errors everywhere and would bias sum_j G w_j, which the
+// singularity subtraction amplifies.  Every 8 sources the float32 partial sums are
+// folded into a per-target two-float (hi, lo) accumulator with an error-free
+// TwoSum.  The SS constant c_i is the float32 high part of f_i, the same value
+// the epilogue uses, so the subtraction telescopes exactly.
+//
+// FP64 kernel (plain form): one field per launch, float64 throughout,
+// absolute coordinates, libm exp and sqrt.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "tagi_internal.cuh"
+
+namespace tagi {
+
+namespace {
+
+constexpr int kThreads32 = 128;
+constexpr int kTPT = 2;  // targets per thread
+constexpr int kTile = 256;
+constexpr int kThreads64 = 256;
+constexpr int kTile64 = 128;
+
+static_assert(kThreads32 * kTPT == kTargetsPerItem, "item size");
+static_assert(kThreads64 == kTargetsPerItem, "item size");
+
+struct KParams {
+    float ky[8];  // -k_o * log2(e) for the Yukawa fields
+    float ga;     // -log2(e) / alpha^2 for the Hartree field
+};
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Error-free transformation: s + e = a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// Every kFold sources, each target's float32 partial sums are folded into its
+// two-float (hi, lo) accumulator by an error-free TwoSum.  Short folds keep
+// the float32 summation error small against the large subtracted term
+// c_i sum_j G w_j, which cancels against the analytic SS term.
+constexpr int kFold = 8;
+template <int NF>
+__device__ __forceinline__ void fold(float (&acc)[kTPT][NF], float (&hi)[kTPT][NF], float (&lo)[kTPT][NF])
+{
+#pragma unroll
+    for (int j = 0; j < kTPT; j++)
+#pragma unroll
+        for (int o = 0; o < NF; o++) {
+            float sum, er;
+            two_sum(hi[j][o], acc[j][o], sum, er);
+            hi[j][o] = sum;
+            lo[j][o] += er;
+        }
+}
+
+// Far field: proxies, single-float positions relative to the batch center;
+//   Yukawa term  e^{-k r} / r * (qh - c w^),  Coulomb term (qh - c w^ e^{-r^2/a^2}) / r.
+template <int NY, bool HH, bool SS>
+__device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const float* __restrict__ sa, int nk,
+                                         const float (&tx)[kTPT], const float (&ty)[kTPT], const float (&tz)[kTPT],
+                                         const float (&nc)[kTPT][NY + HH], float (&hi)[kTPT][NY + HH],
+                                         float (&lo)[kTPT][NY + HH], const KParams& kp)
+{
+    constexpr int NF = NY + HH;
+    for (int k0 = 0; k0 < nk; k0 += kFold) {
+        float acc[kTPT][NF];
+#pragma unroll
+        for (int j = 0; j < kTPT; j++)
+#pragma unroll
+            for (int o = 0; o < NF; o++) acc[j][o] = 0.0f;
+#pragma unroll 2
+        for (int k = k0; k < k0 + kFold; k++) {
+            const float4 s = srec[k];
+            float qv[NF];
+#pragma unroll
+            for (int o = 0; o < NF; o++) qv[o] = sa[o * kTile + k];
+#pragma unroll
+            for (int j = 0; j < kTPT; j++) {
+                const float dx = s.x - tx[j], dy = s.y - ty[j], dz = s.z - tz[j];
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float ri = rsqrt_approx(r2);
+                const float r = r2 * ri;
+#pragma unroll
+                for (int o = 0; o < NY; o++) {
+                    const float e = ex2_approx(kp.ky[o] * r);
+                    const float d = SS ? fmaf(nc[j][o], s.w, qv[o]) : qv[o];
+                    acc[j][o] = fmaf(e * ri, d, acc[j][o]);
+                }
+                if (HH) {
+                    float d;
+                    if (SS) {
+                        const float g = ex2_approx(kp.ga * r2);
+                        d = fmaf(nc[j][NY] * s.w, g, qv[NY]);
+                    } else {
+                        d = qv[NY];
+                    }
+                    acc[j][NY] = fmaf(ri, d, acc[j][NY]);
+                }
+            }
+        }
+        fold<NF>(acc, hi, lo);
+    }
+}
+
+// Near field: mesh points with two-float positions (hi + lo) relative to the
+// batch center and two-float field values f = fh + fl.  The coordinate
+// difference (xh_j - xh_i) + (xl_j - xl_i) and the SS difference
+// (fh_j - c_i) + fl_j, with c_i = fh_i, are exact up to one rounding for close
+// pairs (Sterbenz), so even pairs 1e-5 Bohr apart next to a nucleus keep a
+// relative error of a few float32 ulps.
+//   Yukawa term  e^{-k r} / r * w_j (f_j - c_i),
+//   Coulomb term (rho_j - c_i e^{-r^2/a^2}) w_j / r.
+template <int NY, bool HH, bool SS, bool SELF>
+__device__ __forceinline__ void tile_near(const float4* __restrict__ srec, const float4* __restrict__ slo,
+                                          const float* __restrict__ sa, const float* __restrict__ sb, int nk,
+                                          const float (&tx)[kTPT], const float (&ty)[kTPT], const float (&tz)[kTPT],
+                                          const float (&lx)[kTPT], const float (&ly)[kTPT], const float (&lz)[kTPT],
+                                          const float (&nc)[kTPT][NY + HH], float (&hi)[kTPT][NY + HH],
+                                          float (&lo)[kTPT][NY + HH], const KParams& kp)
+{
+    constexpr int NF = NY + HH;
+    for (int k0 = 0; k0 < nk; k0 += kFold) {
+        float acc[kTPT][NF];
+#pragma unroll
+        for (int j = 0; j < kTPT; j++)
+#pragma unroll
+            for (int o = 0; o < NF; o++) acc[j][o] = 0.0f;
+#pragma unroll 2
+        for (int k = k0; k < k0 + kFold; k++) {
+            const float4 s = srec[k];
+            const float4 sl = slo[k];
+            float fh[NF], fl[NF];
+#pragma unroll
+            for (int o = 0; o < NF; o++) {
+                fh[o] = sa[o * kTile + k];
+                fl[o] = sb[o * kTile + k];
+            }
+#pragma unroll
+            for (int j = 0; j < kTPT; j++) {
+                const float dx = __fadd_rn(__fsub_rn(s.x, tx[j]), __fsub_rn(sl.x, lx[j]));
+                const float dy = __fadd_rn(__fsub_rn(s.y, ty[j]), __fsub_rn(sl.y, ly[j]));
+                const float dz = __fadd_rn(__fsub_rn(s.z, tz[j]), __fsub_rn(sl.z, lz[j]));
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float ri = rsqrt_approx(r2);
+                if (SELF) ri = r2 > 0.0f ? ri : 0.0f;
+                const float r = r2 * ri;
+                const float riw = fmaf(ri, sl.w, ri * s.w);  // ri (w_hi + w_lo)
+#pragma unroll
+                for (int o = 0; o < NY; o++) {
+                    const float e = ex2_approx(kp.ky[o] * r);
+                    const float d = SS ? __fadd_rn(__fadd_rn(fh[o], nc[j][o]), fl[o]) : __fadd_rn(fh[o], fl[o]);
+                    acc[j][o] = fmaf(e * riw, d, acc[j][o]);
+                }
+                if (HH) {
+                    float d;
+                    if (SS) {
+                        const float g = ex2_approx(kp.ga * r2);
+                        d = __fadd_rn(fmaf(nc[j][NY], g, fh[NY]), fl[NY]);
+                    } else {
+                        d = __fadd_rn(fh[NY], fl[NY]);
+                    }
+                    acc[j][NY] = fmaf(riw, d, acc[j][NY]);
+                }
+            }
+        }
+        fold<NF>(acc, hi, lo);
+    }
+}
+
+// two-float x = (h, l) plus float64 offset o, renormalised
+__device__ __forceinline__ void add_offset(float h, float l, double o, float& rh, float& rl)
+{
+    const float oh = (float)o;
+    const float ol = (float)(o - (double)oh);
+    float s, e;
+    two_sum(h, oh, s, e);
+    e = __fadd_rn(e, __fadd_rn(l, ol));
+    rh = __fadd_rn(s, e);
+    rl = __fsub_rn(e, __fsub_rn(rh, s));
+}
+
+template <int NY, bool HH, bool SS>
+__global__ void __launch_bounds__(kThreads32) k_interact32(const Item* __restrict__ items,
+                                                           const Entry* __restrict__ ents,
+                                                           const double* __restrict__ cen,
+                                                           const float4* __restrict__ rec4,
+                                                           const float4* __restrict__ rec4lo,
+                                                           const float* __restrict__ fa, int64_t lda,
+                                                           const float* __restrict__ fb, int64_t ldb, KParams kp,
+                                                           double* __restrict__ part, int nf_tot, int field0)
+{
+    constexpr int NF = NY + HH;
+    __shared__ float4 srec[kTile];
+    __shared__ float4 slo[kTile];
+    __shared__ float sa[NF * kTile];
+    __shared__ float sb[NF * kTile];
+
+    const Item it = items[blockIdx.x];
+    const int tid = threadIdx.x;
+    float tx[kTPT], ty[kTPT], tz[kTPT], lx[kTPT], ly[kTPT], lz[kTPT];
+    float nc[kTPT][NF];
+    float hi[kTPT][NF], lo[kTPT][NF];
+#pragma unroll
+    for (int j = 0; j < kTPT; j++) {
+        const int p = it.t0 + tid + j * kThreads32;
+        const bool ok = p < it.t1;
+        const float4 r = ok ? rec4[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 rl = ok ? rec4lo[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tx[j] = r.x;
+        ty[j] = r.y;
+        tz[j] = r.z;
+        lx[j] = rl.x;
+        ly[j] = rl.y;
+        lz[j] = rl.z;
+#pragma unroll
+        for (int o = 0; o < NF; o++) {
+            nc[j][o] = ok ? -fa[o * lda + p] : 0.0f;  // SS constant c_i = fh_i
+            hi[j][o] = lo[j][o] = 0.0f;
+        }
+    }
+    const double bx = cen[3 * it.batch], by = cen[3 * it.batch + 1], bz = cen[3 * it.batch + 2];
+
+    for (int e = it.e0; e < it.e1; e++) {
+        const Entry en = ents[e];
+        const int f = en.frame;
+        const double ox = cen[3 * f] - bx, oy = cen[3 * f + 1] - by, oz = cen[3 * f + 2] - bz;
+        const bool far = en.flags & 2;
+        const bool self = en.flags & 1;
+        for (int s0 = en.src0; s0 < en.src1; s0 += kTile) {
+            const int ns = min(kTile, en.src1 - s0);
+            const int nk = (ns + 7) & ~7;
+            __syncthreads();
+#pragma unroll
+            for (int h = 0; h < kTile / kThreads32; h++) {
+                const int k = tid + h * kThreads32;
+                if (k < ns) {
+                    float4 r = rec4[s0 + k];
+                    if (far) {
+                        // proxy = cluster center + delta; one rounding to float32
+                        r.x = (float)((double)r.x + ox);
+                        r.y = (float)((double)r.y + oy);
+                        r.z = (float)((double)r.z + oz);
+                    } else {
+                        const float4 rl = rec4lo[s0 + k];
+                        float4 l;
+                        add_offset(r.x, rl.x, ox, r.x, l.x);
+                        add_offset(r.y, rl.y, oy, r.y, l.y);
+                        add_offset(r.z, rl.z, oz, r.z, l.z);
+                        l.w = rl.w;  // low part of the weight
+                        slo[k] = l;
+#pragma unroll
+                        for (int o = 0; o < NF; o++) sb[o * kTile + k] = fb[o * ldb + s0 + k];
+                    }
+                    srec[k] = r;
+#pragma unroll
+                    for (int o = 0; o < NF; o++) sa[o * kTile + k] = fa[o * lda + s0 + k];
+                } else if (k < nk) {
+                    // padding record: far away, zero weight and values -> contributes 0
+                    srec[k] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+                    slo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int o = 0; o < NF; o++) sa[o * kTile + k] = sb[o * kTile + k] = 0.0f;
+                }
+            }
+            __syncthreads();
+            if (far)
+                tile_far<NY, HH, SS>(srec, sa, nk, tx, ty, tz, nc, hi, lo, kp);
+            else if (self)
+                tile_near<NY, HH, SS, true>(srec, slo, sa, sb, nk, tx, ty, tz, lx, ly, lz, nc, hi, lo, kp);
+            else
+                tile_near<NY, HH, SS, false>(srec, slo, sa, sb, nk, tx, ty, tz, lx, ly, lz, nc, hi, lo, kp);
+        }
+    }
+    double* out = part + ((size_t)blockIdx.x * nf_tot + field0) * kTargetsPerItem;
+#pragma unroll
+    for (int j = 0; j < kTPT; j++)
+#pragma unroll
+        for (int o = 0; o < NF; o++) out[o * kTargetsPerItem + tid + j * kThreads32] = (double)hi[j][o] + (double)lo[j][o];
+}
+
+// ---------------------------------------------------------------- bias calibration
+// Mean relative error of the float32 kernel values evaluated exactly as in
+// tile_near / tile_far, against float64, weighted as in the SS integrals:
+//   mode 0: G~ = ex2(ky r) ri, weight r e^{-k r} (int G_k = 1/k^2, k-free in k r)
+//   mode 1: H~ = ex2(ga r^2) ri, weight r e^{-r^2} (int e^{-r^2/a^2}/r = 2 pi a^2)
+// on a deterministic sample of directions and radii.
+constexpr int kCalBlocks = 256, kCalThreads = 256;
+__global__ void k_calibrate(int mode, long long n, double* out)
+{
+    __shared__ double s0[kCalThreads], s1[kCalThreads];
+    const double L2E = 1.4426950408889634;
+    const float ky = (float)(-2.0 * L2E);
+    const double kt = -(double)ky / L2E;
+    const float ga = (float)(-L2E);
+    const double rmax = mode == 0 ? 30.0 / kt : 6.0;
+    double a = 0.0, b = 0.0;
+    for (long long i = blockIdx.x * (long long)kCalThreads + threadIdx.x; i < n; i += (long long)kCalBlocks * kCalThreads) {
+        const double rr = rmax * (i + 0.5) / n;
+        const double th = 2.399963229728653 * i, fz = i * 0.6180339887498949;
+        const double z = -1.0 + 2.0 * (fz - floor(fz));
+        const double sn = sqrt(fmax(0.0, 1.0 - z * z));
+        const float dx = (float)(rr * sn * cos(th)), dy = (float)(rr * sn * sin(th)), dz = (float)(rr * z);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float ri = rsqrt_approx(r2);
+        const double R = sqrt((double)r2);
+        double e, w;
+        if (mode == 0) {
+            const float v = ex2_approx(ky * (r2 * ri)) * ri;
+            const double ref = exp(-kt * R) / R;
+            e = ((double)v - ref) / ref;
+            w = R * exp(-kt * R);
+        } else {
+            const float v = ex2_approx(ga * r2) * ri;
+            const double ref = exp((double)ga * (double)r2 / L2E) / R;  // alpha~ of the rounded ga
+            e = ((double)v - ref) / ref;
+            w = R * exp(-(double)r2);
+        }
+        a += e * w;
+        b += w;
+    }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = kCalThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s0[threadIdx.x] += s0[threadIdx.x + o];
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = s0[0];
+        out[2 * blockIdx.x + 1] = s1[0];
+    }
+}
+
+// ---------------------------------------------------------------- FP64 plain form
+template <int KIND, bool SS>
+__global__ void __launch_bounds__(kThreads64) k_interact64(const Item* __restrict__ items,
+                                                           const Entry* __restrict__ ents,
+                                                           const double* __restrict__ rx, const double* __restrict__ ry,
+                                                           const double* __restrict__ rz, const double* __restrict__ rw,
+                                                           const double* __restrict__ q, const double* __restrict__ c,
+                                                           double kval, double* __restrict__ part, int nf_tot,
+                                                           int field)
+{
+    __shared__ double sx[kTile64], sy[kTile64], sz[kTile64], sw[kTile64], sqv[kTile64];
+    const Item it = items[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int p = it.t0 + tid;
+    const bool ok = p < it.t1;
+    const double x = ok ? rx[p] : 0.0, y = ok ? ry[p] : 0.0, z = ok ? rz[p] : 0.0;
+    const double ci = ok ? c[p] : 0.0;
+    const double ia2 = KIND == 1 ? 1.0 / (kval * kval) : 0.0;
+    double acc = 0.0;
+    for (int e = it.e0; e < it.e1; e++) {
+        const Entry en = ents[e];
+        for (int s0 = en.src0; s0 < en.src1; s0 += kTile64) {
+            const int ns = min(kTile64, en.src1 - s0);
+            __syncthreads();
+            if (tid < ns) {
+                sx[tid] = rx[s0 + tid];
+                sy[tid] = ry[s0 + tid];
+                sz[tid] = rz[s0 + tid];
+                sw[tid] = rw[s0 + tid];
+                sqv[tid] = q[s0 + tid];
+            }
+            __syncthreads();
+            for (int k = 0; k < ns; k++) {
+                const double dx = x - sx[k], dy = y - sy[k], dz = z - sz[k];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 == 0.0) continue;  // the singular r' = r term is skipped
+                const double r = sqrt(r2);
+                if (KIND == 0) {
+                    const double d = SS ? sqv[k] - ci * sw[k] : sqv[k];
+                    acc += exp(-kval * r) / r * d;
+                } else {
+                    const double d = SS ? sqv[k] - ci * sw[k] * exp(-r2 * ia2) : sqv[k];
+                    acc += d / r;
+                }
+            }
+        }
+    }
+    part[((size_t)blockIdx.x * nf_tot + field) * kTargetsPerItem + tid] = acc;
+}
+
+template <int NY, bool HH>
+void launch32_ss(Tree& T, bool ss, const KParams& kp, const float* q, const float* c, double* part, int nf_tot,
+                 int field0)
+{
+    // q: rows of fa (fh for points, qh for proxies), c: rows of fb (fl for points)
+    const int grid = (int)T.nitems;
+    cudaStream_t s = T.stream;
+    if (ss)
+        launch(k_interact32<NY, HH, true>, grid, kThreads32, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
+                                                               T.cl_cen.as<double>(), T.rec4.as<float4>(),
+                                                               T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kp, part,
+                                                               nf_tot, field0);
+    else
+        launch(k_interact32<NY, HH, false>, grid, kThreads32, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
+                                                                T.cl_cen.as<double>(), T.rec4.as<float4>(),
+                                                                T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kp, part,
+                                                                nf_tot, field0);
+    TAGI_LAUNCH_CHECK();
+}
+
+template <bool HH>
+void launch32_ny(int ny, Tree& T, bool ss, const KParams& kp, const float* q, const float* c, double* part,
+                 int nf_tot, int field0)
+{
+    switch (ny) {
+        case 0:
+            if constexpr (HH) launch32_ss<0, true>(T, ss, kp, q, c, part, nf_tot, field0);
+            break;
+        case 1: launch32_ss<1, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
+        case 2: launch32_ss<2, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
+        case 3: launch32_ss<3, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
+        case 4: launch32_ss<4, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
+        case 5: launch32_ss<5, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
+        case 6: launch32_ss<6, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
+        case 7: launch32_ss<7, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
+        case 8:
+            if constexpr (!HH) launch32_ss<8, false>(T, ss, kp, q, c, part, nf_tot, field0);
+            break;
+        default: throw Error(TAGI_ERR_INVALID_ARG, "field group too large");
+    }
+}
+
+}  // namespace
+
+void fp32_bias(cudaStream_t s, double* beta_y, double* beta_g)
+{
+    // measured once per device and process; deterministic
+    static double cache[64][2];
+    static bool done[64] = {false};
+    int dev = 0;
+    TAGI_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!done[dev]) {
+        DevBuf buf;
+        buf.ensure(sizeof(double) * 2 * kCalBlocks);
+        std::vector<double> h(2 * kCalBlocks);
+        for (int mode = 0; mode < 2; mode++) {
+            launch(k_calibrate, kCalBlocks, kCalThreads, 0, s, mode, 1LL << 23, buf.as<double>());
+            TAGI_LAUNCH_CHECK();
+            TAGI_CUDA(cudaMemcpyAsync(h.data(), buf.p, sizeof(double) * 2 * kCalBlocks, cudaMemcpyDeviceToHost, s));
+            TAGI_CUDA(cudaStreamSynchronize(s));
+            double a = 0.0, b = 0.0;
+            for (int i = 0; i < kCalBlocks; i++) {
+                a += h[2 * i];
+                b += h[2 * i + 1];
+            }
+            cache[dev][mode] = a / b;
+        }
+        done[dev] = true;
+    }
+    *beta_y = cache[dev][0];
+    *beta_g = cache[dev][1];
+}
+
+// Float64 value of the decay rate the float32 kernel actually applies:
+// ky = fl32(-k log2 e), k~ = -ky / log2 e.
+double effective_k32(double k)
+{
+    const float ky = (float)(-k * 1.4426950408889634);
+    return -(double)ky / 1.4426950408889634;
+}
+
+// Float64 Gaussian width the float32 kernel applies: ga = fl32(-log2 e / a^2).
+double effective_alpha32(double a)
+{
+    const float ga = (float)(-1.4426950408889634 / (a * a));
+    return sqrt(-1.4426950408889634 / (double)ga);
+}
+
+// Fields [0, nf) of T.q32 / T.c32: Yukawa fields first (kinds[o] == 0), then
+// at most one Coulomb field (kinds[o] == 1) last.  Groups of at most 8 fields
+// share a launch; the Coulomb field joins the last group when it fits.
+void interact32(Tree& T, int nf, const int* kinds, const double* kval, double* part)
+{
+    int ny = 0;
+    while (ny < nf && kinds[ny] == 0) ny++;
+    const bool hh = ny < nf;
+    TAGI_REQUIRE(nf - ny <= 1, "at most one Coulomb field, after the Yukawa fields");
+    const float log2e = 1.4426950408889634f;
+    int o = 0;
+    while (o < nf) {
+        int g_ny = ny - o < 8 ? ny - o : 8;
+        if (g_ny < 0) g_ny = 0;
+        bool g_hh = hh && (o + g_ny == ny) && g_ny < 8;
+        KParams kp{};
+        for (int u = 0; u < g_ny; u++) kp.ky[u] = (float)(-kval[o + u] * 1.4426950408889634);
+        kp.ga = hh ? (float)(-1.4426950408889634 / (kval[ny] * kval[ny])) : 0.0f;
+        (void)log2e;
+        const float* q = T.fa.as<float>() + (size_t)o * T.nrec;
+        const float* c = T.fb.as<float>() + (size_t)o * T.n;
+        if (g_hh)
+            launch32_ny<true>(g_ny, T, T.ss != 0, kp, q, c, part, nf, o);
+        else
+            launch32_ny<false>(g_ny, T, T.ss != 0, kp, q, c, part, nf, o);
+        o += g_ny + (g_hh ? 1 : 0);
+    }
+}
+
+void interact64(Tree& T, int field, int nf_tot, int kind, double kval, const double* q, const double* c,
+                double* part)
+{
+    const int grid = (int)T.nitems;
+    cudaStream_t s = T.stream;
+    const Item* it = T.items.as<Item>();
+    const Entry* en = T.ent.as<Entry>();
+    const double *rx = T.rx.as<double>(), *ry = T.ry.as<double>(), *rz = T.rz.as<double>(), *rw = T.rw.as<double>();
+    if (kind == 0) {
+        if (T.ss)
+            launch(k_interact64<0, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kval, part, nf_tot, field);
+        else
+            launch(k_interact64<0, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kval, part, nf_tot, field);
+    } else {
+        if (T.ss)
+            launch(k_interact64<1, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kval, part, nf_tot, field);
+        else
+            launch(k_interact64<1, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kval, part, nf_tot, field);
+    }
+    TAGI_LAUNCH_CHECK();
+}
+
+}  // namespace tagi

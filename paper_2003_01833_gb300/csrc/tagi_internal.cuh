@@ -1,0 +1,207 @@
+// Internal declarations shared by the translation units of libtagi.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/tagi.h"
+
+namespace tagi {
+
+// ------------------------------------------------------------------ errors
+struct Error : std::runtime_error {
+    tagi_status status;
+    Error(tagi_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define TAGI_CUDA(call)                                                                        \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            throw ::tagi::Error(e_ == cudaErrorMemoryAllocation ? TAGI_ERR_OOM : TAGI_ERR_CUDA, \
+                                std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+#define TAGI_LAUNCH_CHECK() TAGI_CUDA(cudaGetLastError())
+
+#define TAGI_REQUIRE(cond, msg)                                                   \
+    do {                                                                          \
+        if (!(cond)) throw ::tagi::Error(TAGI_ERR_INVALID_ARG, std::string(msg)); \
+    } while (0)
+
+// Device buffer owned by a tree; freed by the tree destructor.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes)
+    {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    DevBuf& operator=(DevBuf&& o) noexcept
+    {
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            o.p = nullptr;
+            o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release();
+    void ensure(size_t nbytes);  // grow (content not kept)
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// Every kernel of the library is launched through launch(), which counts it
+// (tagi_kernel_launches) before the <<<>>> launch.
+void note_launch();
+template <class... KArgs, class... Args>
+inline void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args)
+{
+    note_launch();
+    k<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
+}
+
+// Optional CUDA-event timing of the phases of a call (tagi_profile_*).
+enum ProfGroup { kProfBuild = 0, kProfAnterp = 1, kProfInteract = 2, kProfEpilogue = 3, kProfReduce = 4, kProfN = 5 };
+struct ProfScope {
+    int group;
+    cudaStream_t stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(int g, cudaStream_t s);
+    ~ProfScope();
+};
+
+// Limits
+constexpr int kMaxDepth = 64;
+constexpr int kMaxDegree = 9;
+constexpr int kTargetsPerItem = 256;  // targets of one work item (one CTA)
+constexpr int kAntChunk = 2048;       // points per anterpolation work item
+
+// Interaction entry: a contiguous range of source records [src0, src1) seen
+// from a batch.  frame: cluster whose center the records' local coordinates
+// are relative to (FP32 path).  flags bit0: the range holds the batch's own
+// points (self pair possible); bit1: proxies (far field).
+struct Entry {
+    int src0, src1, frame, flags;
+};
+
+// Work item of the near/far kernel: targets [t0, t1) of batch `batch`
+// (tree positions), list entries [e0, e1).
+struct Item {
+    int t0, t1, e0, e1;
+    int batch, tchunk, pad0, pad1;
+};
+
+// Anterpolation work item: positions [p0, p1) of cluster `cluster`, whose
+// proxies are record block `far` (index among approximated clusters).
+struct AntItem {
+    int p0, p1, cluster, far;
+};
+
+struct Tree {
+    // parameters
+    int64_t n = 0;
+    double theta = 0.7;
+    int degree = 6;
+    int leaf_size = 2000;
+    int prec = TAGI_FP32C;
+    int ss = 1;
+    double alpha = 1.0;
+    int P = 0;  // (degree+1)^3
+    cudaStream_t stream = nullptr;
+
+    // sizes
+    int nc = 0, nleaf = 0, depth = 0, nfar = 0;
+    int64_t nent = 0, nitems = 0, ntchunk = 0, nant = 0, nrec = 0;
+    int64_t near_pairs = 0, far_pairs = 0;
+
+    // points in tree order
+    DevBuf perm;             // int[n] tree position -> caller index
+    DevBuf px, py, pz, pw;   // double[n]
+    DevBuf pt_leaf;          // int[n] leaf (batch) cluster owning each position
+
+    // clusters
+    DevBuf cl_begin, cl_end, cl_parent, cl_level, cl_nchild, cl_child;  // int
+    DevBuf cl_lo, cl_hi, cl_cen;                                         // double[3*nc]
+    DevBuf cl_rad;                                                       // double[nc]
+    DevBuf cl_far;   // int[nc]: index among approximated clusters, or -1
+    DevBuf leaves;   // int[nleaf]
+    DevBuf far_cl;   // int[nfar]
+
+    // lists (expanded): entries in batch order with CSR offsets by leaf index
+    DevBuf ent;       // Entry[nent]
+    DevBuf ent_off;   // int64 -> int[nleaf+1]
+    DevBuf ent_batch; // int[nent] (leaf cluster id), for export
+    DevBuf ent_clus;  // int[nent] (source cluster id: leaf for direct, cluster for far)
+
+    // work items
+    DevBuf items;       // Item[nitems]
+    DevBuf tc_item0;    // int[ntchunk+1]: first item of each target chunk
+    DevBuf tc_t0, tc_t1, tc_batch;  // int[ntchunk]
+    DevBuf ant_items;   // AntItem[nant]
+    DevBuf far_ant0;    // int[nfar+1]: first anterpolation item of each far cluster
+
+    // source records (points then proxies), nrec = n + nfar * P
+    DevBuf rec4;        // FP32C: float4 (dx, dy, dz, w) relative to frame center (high parts)
+    DevBuf rec4lo;      // FP32C: float4 low parts of (dx, dy, dz) for the n mesh points
+    DevBuf rx, ry, rz, rw;  // FP64: absolute coordinates and weight
+    // per-call work buffers
+    DevBuf fa;          // float [nf][nrec]: fh = f rounded (points), qh (proxies)
+    DevBuf fb;          // float [nf][n]: fl = f - fh (points)
+    DevBuf qant;        // float [nf][n]: f w rounded, the anterpolation input
+    DevBuf q64;         // double [nf][nrec]
+    DevBuf c64;         // double [nf][n] field values in tree order (FP64 SS constants)
+    DevBuf wc;          // double [n] quadrature weights in the caller's order
+    DevBuf part;        // double partial sums
+    DevBuf antpart;     // double anterpolation partials
+    DevBuf scratch;     // general scratch (reductions)
+    DevBuf fbuf;        // double [nf][n] formed fields (Green step)
+    DevBuf ubuf;        // double [nf][n] convolution results (Green step)
+
+};
+
+// tree.cu
+void build_tree(Tree& T, const double* xyz, const double* w);
+// anterp.cu
+void anterpolate_weights(Tree& T);  // w^ for every approximated cluster (FP32C and FP64)
+void anterpolate_fields32(Tree& T, int nf);  // q^ rows [0, nf) of T.fa from T.qant
+void anterpolate_fields64(Tree& T, int nf);
+void anterpolate_all_clusters64(Tree& T, const double* q, int nq, double* qh);
+// interact.cu
+// kinds[o]: 0 = Yukawa with kval[o], 1 = Coulomb/Hartree
+void interact32(Tree& T, int nf, const int* kinds, const double* kval, double* part);
+void interact64(Tree& T, int field, int nf_tot, int kind, double kval, const double* q, const double* c,
+                double* part);
+// mean relative bias of the float32 Yukawa and Gaussian kernel values (measured)
+void fp32_bias(cudaStream_t s, double* beta_y, double* beta_g);
+double effective_k32(double k);
+double effective_alpha32(double a);
+// green.cu
+void prepare_points32(Tree& T, const double* f, int nf);   // fa, fb, qant from caller-order fields
+void prepare_points64(Tree& T, const double* f, int nf);   // q64 from caller-order fields
+// u[o][caller i] for o in [0, nf): kinds[o] 0 = Yukawa (k = kval[o]), 1 = Coulomb (alpha = kval[o]).
+// out[o] points to the caller-order output row of field o.
+void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* kval, const double* part,
+                     double* const* out);
+// Green step reductions on caller-order rows (all float64):
+//   f (nw x n), psi (nw x n, in: old, out: new), u (nw x n, in: Yukawa results,
+//   clobbered), eps_s (host, shifted eigenvalues, updated), resid (host or null).
+void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, double* eps_s, double* resid);
+double weighted_dot(Tree& T, const double* a, const double* b);
+
+// scan helper (exclusive) on device, single CTA: out[i] = sum_{j<i} in[j], out[n] = total
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
+}  // namespace tagi

@@ -1,0 +1,297 @@
+"""Python binding of libtagi (ctypes).
+
+Argument marshalling only: every function here passes device pointers, sizes
+and the current CUDA stream to the C ABI declared in ``include/tagi.h`` and
+raises ``TagiError`` on a non-zero status.  No arithmetic of the method runs
+in Python.  PyTorch provides the device memory and the stream.
+
+The shared library must have been built in-tree (``__graft_entry__.build()``
+or ``python paper_2003_01833_gb300/build.py``); importing a function whose
+library is missing raises immediately -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtagi.so")
+
+TAGI_OK = 0
+TAGI_ERR_INVALID_ARG = 1
+TAGI_ERR_CUDA = 2
+TAGI_ERR_OOM = 3
+TAGI_ERR_TIMEOUT = 4
+TAGI_ERR_STATE = 5
+TAGI_FP64 = 0
+TAGI_FP32C = 1
+
+
+class TagiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"tagi status {status}: {msg}")
+        self.status = status
+
+
+class tagi_params(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("degree", ctypes.c_int), ("leaf_size", ctypes.c_int),
+                ("batch_size", ctypes.c_int), ("prec", ctypes.c_int), ("ss", ctypes.c_int),
+                ("alpha", ctypes.c_double)]
+
+
+class tagi_tree_stats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_clusters", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("n_far_clusters", ctypes.c_int32),
+                ("n_list_entries", ctypes.c_int64), ("n_items", ctypes.c_int64),
+                ("near_pairs", ctypes.c_int64), ("far_pairs", ctypes.c_int64), ("degree", ctypes.c_int32),
+                ("n_proxies", ctypes.c_int32)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    """Load libtagi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.tagi_tree_build.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.POINTER(tagi_params), _vp,
+                                      ctypes.POINTER(_vp)]
+        L.tagi_tree_destroy.argtypes = [_vp]
+        L.tagi_tree_info.argtypes = [_vp, ctypes.POINTER(tagi_tree_stats)]
+        L.tagi_tree_export.argtypes = [_vp, _I32, _I32, _I32, _D, _D, _I32, _I32, _I32]
+        L.tagi_tree_lists.argtypes = [_vp, ctypes.c_int64, _I32, _I32, _I32, _I64]
+        L.tagi_anterpolate.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp]
+        L.tagi_yukawa_conv.argtypes = [_vp, _vp, _D, ctypes.c_int, _vp, _vp]
+        L.tagi_coulomb_conv.argtypes = [_vp, _vp, _vp, _vp]
+        L.tagi_green_step.argtypes = [_vp, _vp, ctypes.c_double, _vp, _D, ctypes.c_int, _vp, _vp, _D, _D, _vp]
+        L.tagi_kernel_launches.restype = ctypes.c_int64
+        L.tagi_profile_enable.argtypes = [ctypes.c_int]
+        L.tagi_fp32_bias.argtypes = [_D, _D, _vp]
+        L.tagi_profile_read.argtypes = [ctypes.c_int, _D, _I64]
+        L.tagi_last_error.restype = ctypes.c_char_p
+        L.tagi_version.restype = ctypes.c_char_p
+        for name in ("tagi_tree_build", "tagi_tree_destroy", "tagi_tree_info", "tagi_tree_export",
+                     "tagi_tree_lists", "tagi_anterpolate", "tagi_yukawa_conv", "tagi_coulomb_conv",
+                     "tagi_green_step", "tagi_profile_enable", "tagi_profile_read", "tagi_fp32_bias"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != TAGI_OK:
+        raise TagiError(status, lib().tagi_last_error().decode())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t, name, numel=None):
+    """Device pointer of a contiguous float64 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hd(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_D)
+
+
+def make_params(theta=0.7, degree=8, leaf_size=2000, prec=TAGI_FP32C, ss=True, alpha=1.0):
+    return tagi_params(float(theta), int(degree), int(leaf_size), int(leaf_size), int(prec), int(bool(ss)),
+                       float(alpha))
+
+
+# ----------------------------------------------------------------- C ABI names
+def tagi_tree_build(xyz, w, params, stream=None):
+    """xyz: (3, n) float64 CUDA tensor, w: (n,) float64 CUDA tensor."""
+    n = w.numel()
+    h = ctypes.c_void_p()
+    _check(lib().tagi_tree_build(_dptr(xyz, "xyz", 3 * n), _dptr(w, "w", n), n, ctypes.byref(params),
+                                 _stream(stream), ctypes.byref(h)))
+    _SIZES[h.value] = tagi_tree_info(h)
+    return h
+
+
+_SIZES: dict = {}  # handle -> sizes, so the size checks below need no device sync
+
+
+def _sizes(tree):
+    key = tree.value if isinstance(tree, ctypes.c_void_p) else tree
+    if key not in _SIZES:
+        _SIZES[key] = tagi_tree_info(tree)
+    return _SIZES[key]
+
+
+def _tree_n(tree):
+    return _sizes(tree)["n_points"]
+
+
+def tagi_tree_destroy(tree):
+    key = tree.value if isinstance(tree, ctypes.c_void_p) else tree
+    _SIZES.pop(key, None)
+    _check(lib().tagi_tree_destroy(tree))
+
+
+def tagi_tree_info(tree):
+    st = tagi_tree_stats()
+    _check(lib().tagi_tree_info(tree, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in tagi_tree_stats._fields_}
+
+
+def tagi_tree_export(tree):
+    info = tagi_tree_info(tree)
+    n, nc = info["n_points"], info["n_clusters"]
+    perm = np.empty(n, np.int32)
+    begin = np.empty(nc, np.int32)
+    end = np.empty(nc, np.int32)
+    lo = np.empty((nc, 3))
+    hi = np.empty((nc, 3))
+    parent = np.empty(nc, np.int32)
+    nchild = np.empty(nc, np.int32)
+    child = np.empty((nc, 8), np.int32)
+    p32 = lambda a: a.ctypes.data_as(_I32)
+    _check(lib().tagi_tree_export(tree, p32(perm), p32(begin), p32(end), lo.ctypes.data_as(_D),
+                                  hi.ctypes.data_as(_D), p32(parent), p32(nchild), p32(child)))
+    return dict(perm=perm, begin=begin, end=end, lo=lo, hi=hi, parent=parent, nchild=nchild, child=child)
+
+
+def tagi_tree_lists(tree):
+    cnt = ctypes.c_int64()
+    _check(lib().tagi_tree_lists(tree, 0, None, None, None, ctypes.byref(cnt)))
+    m = cnt.value
+    b, c, k = np.empty(m, np.int32), np.empty(m, np.int32), np.empty(m, np.int32)
+    p32 = lambda a: a.ctypes.data_as(_I32)
+    _check(lib().tagi_tree_lists(tree, m, p32(b), p32(c), p32(k), ctypes.byref(cnt)))
+    return b, c, k
+
+
+def tagi_anterpolate(tree, q, qh, stream=None):
+    """q: (nq, n) float64 CUDA; qh: (n_clusters, nq, P) float64 CUDA (output)."""
+    nq = q.shape[0] if q.dim() == 2 else 1
+    info = _sizes(tree)
+    if q.numel() != nq * info["n_points"]:
+        raise ValueError("q must have nq * n elements")
+    if qh.numel() != info["n_clusters"] * nq * info["n_proxies"]:
+        raise ValueError("qh must have n_clusters * nq * (degree+1)^3 elements")
+    _check(lib().tagi_anterpolate(tree, _dptr(q, "q"), nq, _dptr(qh, "qh"), _stream(stream)))
+
+
+def tagi_yukawa_conv(tree, f, k, u, stream=None):
+    """f, u: (nf, n) float64 CUDA tensors; k: nf host floats."""
+    nf = f.shape[0] if f.dim() == 2 else 1
+    if f.numel() != nf * _tree_n(tree):
+        raise ValueError("f must have nf * n elements")
+    ka, kp = _hd(np.atleast_1d(k))
+    if ka.size != nf:
+        raise ValueError("one k per field")
+    _check(lib().tagi_yukawa_conv(tree, _dptr(f, "f"), kp, nf, _dptr(u, "u", f.numel()), _stream(stream)))
+
+
+def tagi_coulomb_conv(tree, rho, vh, stream=None):
+    if rho.numel() != _tree_n(tree):
+        raise ValueError("rho must have n elements")
+    _check(lib().tagi_coulomb_conv(tree, _dptr(rho, "rho"), _dptr(vh, "vh", rho.numel()), _stream(stream)))
+
+
+def tagi_green_step(tree, veff, vshift, psi, eps, rho=None, vh=None, stream=None):
+    """psi: (nw, n) float64 CUDA, updated in place; eps: nw host floats.
+
+    Returns (eps_new, resid, eh) as NumPy values (eh is None without rho)."""
+    nw = psi.shape[0] if psi.dim() == 2 else 1
+    n = _tree_n(tree)
+    if psi.numel() != nw * n or veff.numel() != n or (rho is not None and (rho.numel() != n or vh is None
+                                                                           or vh.numel() != n)):
+        raise ValueError("psi must be (nw, n); veff, rho and vh must have n elements")
+    ea, ep = _hd(np.atleast_1d(eps).copy())
+    if ea.size != nw:
+        raise ValueError("one eigenvalue per orbital")
+    res = np.zeros(nw)
+    eh = np.zeros(1)
+    _check(lib().tagi_green_step(tree, _dptr(veff, "veff"), float(vshift), _dptr(psi, "psi"), ep, nw,
+                                 _dptr(rho, "rho"), _dptr(vh, "vh"), res.ctypes.data_as(_D),
+                                 eh.ctypes.data_as(_D) if rho is not None else None, _stream(stream)))
+    return ea, res, (float(eh[0]) if rho is not None else None)
+
+
+PROFILE_GROUPS = {"build": 0, "anterp": 1, "interact": 2, "epilogue": 3, "reduce": 4}
+
+
+def tagi_kernel_launches():
+    return int(lib().tagi_kernel_launches())
+
+
+def tagi_profile_enable(on=True):
+    _check(lib().tagi_profile_enable(int(bool(on))))
+
+
+def tagi_profile_read(group):
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    g = PROFILE_GROUPS[group] if isinstance(group, str) else int(group)
+    _check(lib().tagi_profile_read(g, ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def tagi_fp32_bias(stream=None):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().tagi_fp32_bias(ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+    return a.value, b.value
+
+
+def tagi_last_error():
+    return lib().tagi_last_error().decode()
+
+
+def tagi_version():
+    return lib().tagi_version().decode()
+
+
+class Tree:
+    """Owning wrapper of a tagi_tree handle."""
+
+    def __init__(self, xyz, w, **params):
+        self.params = make_params(**params)
+        self.handle = tagi_tree_build(xyz, w, self.params)
+        self.n = w.numel()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tagi_tree_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self):
+        return tagi_tree_info(self.handle)

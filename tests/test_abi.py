@@ -1,0 +1,58 @@
+"""The C-ABI library loads and exports every entry point include/tagi.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    txt = open(os.path.join(ROOT, "include", "tagi.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tagi_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2003_01833_gb300 import build as B
+
+    B.build()
+    return ctypes.CDLL(B.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for n in ("tagi_tree_build", "tagi_anterpolate", "tagi_yukawa_conv", "tagi_coulomb_conv", "tagi_green_step"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in declared():
+        assert hasattr(lib, n), n
+
+
+def test_version_and_error_without_gpu(lib):
+    lib.tagi_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.tagi_version()
+    lib.tagi_last_error.restype = ctypes.c_char_p
+    assert isinstance(lib.tagi_last_error(), bytes)
+
+
+def test_argument_validation_needs_no_gpu(lib):
+    """Bad arguments are rejected before any device work."""
+    import paper_2003_01833_gb300.tagi as T
+
+    h = ctypes.c_void_p()
+    p = T.make_params(theta=1.5)
+    st = lib.tagi_tree_build(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_int64(10), ctypes.byref(p), None,
+                             ctypes.byref(h))
+    assert st == T.TAGI_ERR_INVALID_ARG
+    p = T.make_params(degree=12)
+    assert lib.tagi_tree_build(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_int64(10), ctypes.byref(p), None,
+                               ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+    assert lib.tagi_tree_destroy(None) == T.TAGI_OK
+    lib.tagi_yukawa_conv.argtypes = [ctypes.c_void_p] * 6
+    assert lib.tagi_yukawa_conv(None, None, None, 1, None, None) == T.TAGI_ERR_INVALID_ARG
