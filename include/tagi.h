@@ -190,6 +190,30 @@ tagi_status tagi_fp32_bias(double* beta_yukawa, double* beta_gauss, void* stream
 tagi_status tagi_profile_enable(int on);
 tagi_status tagi_profile_read(int group, double* ms, int64_t* count);
 
+/* Direct-sum Yukawa convolution that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code recording a CUDA graph, host frameworks that
+ * own every device byte through their own memory pool and forbid hidden
+ * allocations, latency-critical loops that cannot take an allocation's
+ * implicit synchronisation.  It computes, in float64, the same sum as
+ * tagi_yukawa_conv with singularity subtraction on a tree with theta = 0:
+ *   u[o][i] = sum_{j, r_ij != 0} G_{k_o}(r_ij) (f[o][j] - f[o][i]) w_j + f[o][i] / k_o^2,
+ * G_k(r) = exp(-k r) / (4 pi r), over all n points (O(n^2) work).
+ *   xyz [dev] 3*n float64 (structure of arrays), w [dev] n, f [dev] nf*n,
+ *   k [host] nf (finite, > 0), u [dev] nf*n, caller-owned; 1 <= nf <= 16.
+ * Scratch: one file-scope device array of 2^20 float64 values (8 MiB), held
+ * by every GPU that loads the library until the process exits.  Calls with
+ * n * nf > 1048576 are rejected with TAGI_ERR_INVALID_ARG.  All calls share
+ * that array and it keeps the last call's contents: two calls whose work
+ * overlaps on the GPU (different streams, or different host threads on the
+ * same device) race and give wrong results; serialise them.  Each call writes
+ * every scratch value it reads, so stale contents are never used.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Enqueued on `stream`, asynchronous. */
+tagi_status tagi_yukawa_direct_noalloc(const double* xyz, const double* w, const double* f, const double* k,
+                                       int nf, int64_t n, double* u, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* tagi_last_error(void);
 

@@ -74,6 +74,16 @@ tagi_status fail(const Error& e)
     return e.status;
 }
 
+}  // namespace
+
+tagi_status report_error(tagi_status status, const char* msg)
+{
+    g_err = msg;
+    return status;
+}
+
+namespace {
+
 template <class F>
 tagi_status guarded(F&& f)
 {

@@ -201,6 +201,9 @@ void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* kval, cons
 void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, double* eps_s, double* resid);
 double weighted_dot(Tree& T, const double* a, const double* b);
 
+// sets the message tagi_last_error returns on this thread; returns status
+tagi_status report_error(tagi_status status, const char* msg);
+
 // scan helper (exclusive) on device, single CTA: out[i] = sum_{j<i} in[j], out[n] = total
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 

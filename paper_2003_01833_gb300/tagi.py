@@ -76,6 +76,8 @@ def lib():
         L.tagi_kernel_launches.restype = ctypes.c_int64
         L.tagi_profile_enable.argtypes = [ctypes.c_int]
         L.tagi_fp32_bias.argtypes = [_D, _D, _vp]
+        L.tagi_yukawa_direct_noalloc.argtypes = [_vp, _vp, _vp, _D, ctypes.c_int, ctypes.c_int64, _vp, _vp]
+        L.tagi_yukawa_direct_noalloc.restype = ctypes.c_int
         L.tagi_profile_read.argtypes = [ctypes.c_int, _D, _I64]
         L.tagi_last_error.restype = ctypes.c_char_p
         L.tagi_version.restype = ctypes.c_char_p
@@ -258,6 +260,19 @@ def tagi_fp32_bias(stream=None):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().tagi_fp32_bias(ctypes.byref(a), ctypes.byref(b), _stream(stream)))
     return a.value, b.value
+
+
+def tagi_yukawa_direct_noalloc(xyz, w, f, k, u, stream=None):
+    """Direct-sum Yukawa convolution without any device allocation (see
+    include/tagi.h).  xyz (3, n), w (n,), f and u (nf, n): float64 CUDA
+    tensors; k: nf host floats."""
+    n = w.numel()
+    nf = f.shape[0] if f.dim() == 2 else 1
+    ka, kp = _hd(np.atleast_1d(k))
+    if ka.size != nf:
+        raise ValueError("one k per field")
+    _check(lib().tagi_yukawa_direct_noalloc(_dptr(xyz, "xyz", 3 * n), _dptr(w, "w", n), _dptr(f, "f", nf * n), kp,
+                                            nf, n, _dptr(u, "u", nf * n), _stream(stream)))
 
 
 def tagi_last_error():
