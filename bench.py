@@ -115,17 +115,19 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline model
 # Thread instructions issued per pair in the FP32C kernel, counted from the
-# source of tile_near / tile_far (FP32 pipe + MUFU; shared-memory loads and
-# loop overhead excluded).  Near: two-float coordinate difference 9, r^2 3,
-# rsqrt 1, r 1, r*w 1 -> 15 per pair; per Yukawa field k r 1, ex2 1, SS
-# difference 2, e*riw 1, accumulate 1 -> 6; Hartree 1 + 1 + 2 + 1 -> 5.
-# Far: difference 3, r^2 3, rsqrt 1, r 1 -> 8; per Yukawa field 1 + 1 + 1 + 1
-# + 1 -> 5; Hartree 1 + 1 + 1 + 1 + 1 -> 5.
+# source of tile_near / tile_far (FP32 pipe + MUFU; shared-memory loads, the
+# self-pair mask, the two-float folds and loop overhead excluded).
+# Near, per pair: difference 3, r^2 3, rsqrt 1, r 1, r (w_hi + w_lo) 2 -> 10;
+# per Yukawa field: k r 1, ex2 1, SS difference 2, e r w 1, accumulate 1 -> 6;
+# Hartree: a r^2 1, ex2 1, c g subtraction 1, + f_lo 1, accumulate 1 -> 5.
+# Far, per pair: difference 3, r^2 3, rsqrt 1, r 1 -> 8; per Yukawa field:
+# k r 1, ex2 1, q - c w 1, e / r 1, accumulate 1 -> 5; Hartree: a r^2 1,
+# ex2 1, c w 1, subtraction 1, accumulate 1 -> 5.
 ISSUE_PER_SM_CLK = 128  # 4 schedulers x 32 lanes, one warp instruction each per clock
 
 
 def issue_per_pair(ny, hh):
-    near = 15 + 6 * ny + (5 if hh else 0)
+    near = 10 + 6 * ny + (5 if hh else 0)
     far = 8 + 5 * ny + (5 if hh else 0)
     return near, far
 

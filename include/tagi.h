@@ -179,6 +179,12 @@ tagi_status tagi_green_step(tagi_tree* tree, const double* veff, double vshift, 
  * events.  ms, count [host], either may be NULL. */
 int64_t tagi_kernel_launches(void);
 
+/* Device memory of trees and calls comes from a caching allocator: blocks a
+ * tree or a call gives back are kept for later calls on the same stream.
+ * tagi_trim_cache synchronises the device and returns every cached block to
+ * the driver (call it after destroying trees to shrink the footprint). */
+tagi_status tagi_trim_cache(void);
+
 /* Mean relative bias of the float32 kernel values of the TAGI_FP32C path on
  * the current device, weighted as in the singularity-subtraction integrals:
  * *beta_yukawa for exp(-k r)/r (weight r e^{-k r}), *beta_gauss for

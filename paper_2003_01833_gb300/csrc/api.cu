@@ -14,22 +14,6 @@
 
 namespace tagi {
 
-void DevBuf::release()
-{
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-}
-
-void DevBuf::ensure(size_t nbytes)
-{
-    if (nbytes <= bytes && p) return;
-    release();
-    if (nbytes == 0) nbytes = 16;
-    TAGI_CUDA(cudaMalloc(&p, nbytes));
-    bytes = nbytes;
-}
-
 void form_fields(Tree& T, const double* veff, double vshift, const double* psi, int nw, double* f);
 
 namespace {
@@ -181,6 +165,7 @@ tagi_status tagi_profile_enable(int on)
 tagi_status tagi_fp32_bias(double* beta_yukawa, double* beta_gauss, void* stream)
 {
     return guarded([&] {
+        AllocStream as((cudaStream_t)stream);
         double a = 0.0, b = 0.0;
         fp32_bias((cudaStream_t)stream, &a, &b);
         if (beta_yukawa) *beta_yukawa = a;
@@ -235,6 +220,7 @@ tagi_status tagi_tree_build(const double* xyz, const double* w, int64_t n, const
         T->alpha = p.alpha;
         T->P = (p.degree + 1) * (p.degree + 1) * (p.degree + 1);
         T->stream = (cudaStream_t)stream;
+        AllocStream as(T->stream);
         ProfScope ps(kProfBuild, T->stream);
         build_tree(*T, xyz, w);
         T->wc.ensure(8 * (size_t)n);
@@ -249,7 +235,9 @@ tagi_status tagi_tree_destroy(tagi_tree* tree)
     return guarded([&] {
         if (!tree) return;
         Tree* T = reinterpret_cast<Tree*>(tree);
-        cudaStreamSynchronize(T->stream);
+        // the tree's buffers may have served calls on several streams; wait
+        // for all of them before the blocks go back to the cache
+        cudaDeviceSynchronize();
         delete T;
     });
 }
@@ -320,6 +308,7 @@ tagi_status tagi_anterpolate(tagi_tree* tree, const double* q, int nq, double* q
         TAGI_REQUIRE(q != nullptr && qh != nullptr, "q or qh is NULL");
         TAGI_REQUIRE(nq >= 1, "nq must be >= 1");
         T->stream = (cudaStream_t)stream;
+        AllocStream as(T->stream);
         anterpolate_all_clusters64(*T, q, nq, qh);
     });
 }
@@ -332,6 +321,7 @@ tagi_status tagi_yukawa_conv(tagi_tree* tree, const double* f, const double* k, 
         TAGI_REQUIRE(nf >= 1, "nf must be >= 1");
         for (int o = 0; o < nf; o++) TAGI_REQUIRE(std::isfinite(k[o]) && k[o] > 0.0, "every k must be finite and > 0");
         T->stream = (cudaStream_t)stream;
+        AllocStream as(T->stream);
         std::vector<int> kinds(nf, 0);
         std::vector<double> kv(k, k + nf);
         std::vector<double*> out(nf);
@@ -346,6 +336,7 @@ tagi_status tagi_coulomb_conv(tagi_tree* tree, const double* rho, double* vh, vo
         Tree* T = as_tree(tree);
         TAGI_REQUIRE(rho != nullptr && vh != nullptr, "rho or vh is NULL");
         T->stream = (cudaStream_t)stream;
+        AllocStream as(T->stream);
         int kind = 1;
         double a = T->alpha;
         double* out = vh;
@@ -368,6 +359,7 @@ tagi_status tagi_green_step(tagi_tree* tree, const double* veff, double vshift, 
             TAGI_REQUIRE(std::isfinite(es[o]) && es[o] < 0.0, "eps + vshift must be negative (Section 3.3)");
         }
         T->stream = (cudaStream_t)stream;
+        AllocStream as(T->stream);
         const int64_t n = T->n;
         const int nf = nw + (rho ? 1 : 0);
         T->fbuf.ensure(sizeof(double) * (size_t)nf * n);

@@ -14,11 +14,12 @@
 //
 // FP32C kernel: all fields of a call (each Yukawa field with its own k, plus
 // the Hartree field) share one pass over the geometry.  Each CTA owns up to
-// 256 targets of one batch (128 threads x 2 targets) and a contiguous segment
+// 256 targets of one batch (64 threads x 4 targets, or 128 x 2 for launches
+// with more than 4 fields) and a contiguous segment
 // of the batch's interaction list; source tiles of 256 records are staged in
 // shared memory with positions shifted from the record's frame (its leaf or
-// cluster center) to the batch center.  Near-field records are two-float
-// (position and field value, see tile_near); proxies are single float.
+// cluster center) to the batch center in float64 and rounded once.  Near-field
+// values and weights are two-float (see tile_near); proxies are single float.
 // rsqrt and exp2 use the MUFU unit (rsqrt.approx, ex2.approx); their mean
 // bias is measured once per device (fp32_bias) and compensated in the SS
 // epilogue.  Quadrature weights of mesh points are two-float too: adaptive
@@ -42,13 +43,17 @@ namespace tagi {
 
 namespace {
 
-constexpr int kThreads32 = 128;
-constexpr int kTPT = 2;  // targets per thread
 constexpr int kTile = 256;
+// targets per thread: 4 for launches with at most 4 fields, 2 above (register
+// pressure); the CTA always owns kTargetsPerItem targets
+template <int NF>
+struct Tpt {
+    static constexpr int value = NF <= 4 ? 4 : 2;
+    static constexpr int threads = kTargetsPerItem / value;
+};
 constexpr int kThreads64 = 256;
 constexpr int kTile64 = 128;
 
-static_assert(kThreads32 * kTPT == kTargetsPerItem, "item size");
 static_assert(kThreads64 == kTargetsPerItem, "item size");
 
 struct KParams {
@@ -82,11 +87,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 // the float32 summation error small against the large subtracted term
 // c_i sum_j G w_j, which cancels against the analytic SS term.
 constexpr int kFold = 8;
-template <int NF>
-__device__ __forceinline__ void fold(float (&acc)[kTPT][NF], float (&hi)[kTPT][NF], float (&lo)[kTPT][NF])
+template <int NF, int TPT>
+__device__ __forceinline__ void fold(float (&acc)[TPT][NF], float (&hi)[TPT][NF], float (&lo)[TPT][NF])
 {
 #pragma unroll
-    for (int j = 0; j < kTPT; j++)
+    for (int j = 0; j < TPT; j++)
 #pragma unroll
         for (int o = 0; o < NF; o++) {
             float sum, er;
@@ -96,29 +101,53 @@ __device__ __forceinline__ void fold(float (&acc)[kTPT][NF], float (&hi)[kTPT][N
         }
 }
 
+// Shared-memory layout of a staged tile: per source one float4 of position
+// (relative to the batch center) and weight (high part), and the values
+// packed four to a float4: components [0, NF) hold fh (points) or qh
+// (proxies), components [NF, 2 NF) hold fl and component 2 NF the low part of
+// the weight (points only).
+template <int NF>
+struct TileLayout {
+    static constexpr int G = (2 * NF + 4) / 4;  // float4 groups of values per source
+};
+
+template <int NF>
+__device__ __forceinline__ void load_values(const float4* __restrict__ sv, int k, float (&v)[4 * TileLayout<NF>::G])
+{
+    constexpr int G = TileLayout<NF>::G;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const float4 t = sv[g * kTile + k];
+        v[4 * g] = t.x;
+        v[4 * g + 1] = t.y;
+        v[4 * g + 2] = t.z;
+        v[4 * g + 3] = t.w;
+    }
+}
+
 // Far field: proxies, single-float positions relative to the batch center;
 //   Yukawa term  e^{-k r} / r * (qh - c w^),  Coulomb term (qh - c w^ e^{-r^2/a^2}) / r.
-template <int NY, bool HH, bool SS>
-__device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const float* __restrict__ sa, int nk,
-                                         const float (&tx)[kTPT], const float (&ty)[kTPT], const float (&tz)[kTPT],
-                                         const float (&nc)[kTPT][NY + HH], float (&hi)[kTPT][NY + HH],
-                                         float (&lo)[kTPT][NY + HH], const KParams& kp)
+template <int NY, bool HH, bool SS, int TPT>
+__device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const float4* __restrict__ sv, int nk,
+                                         const float (&tx)[TPT], const float (&ty)[TPT], const float (&tz)[TPT],
+                                         const float (&nc)[TPT][NY + HH], float (&hi)[TPT][NY + HH],
+                                         float (&lo)[TPT][NY + HH], const KParams& kp)
 {
     constexpr int NF = NY + HH;
+    constexpr int G = TileLayout<NF>::G;
     for (int k0 = 0; k0 < nk; k0 += kFold) {
-        float acc[kTPT][NF];
+        float acc[TPT][NF];
 #pragma unroll
-        for (int j = 0; j < kTPT; j++)
+        for (int j = 0; j < TPT; j++)
 #pragma unroll
             for (int o = 0; o < NF; o++) acc[j][o] = 0.0f;
 #pragma unroll 2
         for (int k = k0; k < k0 + kFold; k++) {
             const float4 s = srec[k];
-            float qv[NF];
+            float qv[4 * G];
+            load_values<NF>(sv, k, qv);
 #pragma unroll
-            for (int o = 0; o < NF; o++) qv[o] = sa[o * kTile + k];
-#pragma unroll
-            for (int j = 0; j < kTPT; j++) {
+            for (int j = 0; j < TPT; j++) {
                 const float dx = s.x - tx[j], dy = s.y - ty[j], dz = s.z - tz[j];
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 const float ri = rsqrt_approx(r2);
@@ -141,89 +170,68 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const 
                 }
             }
         }
-        fold<NF>(acc, hi, lo);
+        fold<NF, TPT>(acc, hi, lo);
     }
 }
 
-// Near field: mesh points with two-float positions (hi + lo) relative to the
-// batch center and two-float field values f = fh + fl.  The coordinate
-// difference (xh_j - xh_i) + (xl_j - xl_i) and the SS difference
-// (fh_j - c_i) + fl_j, with c_i = fh_i, are exact up to one rounding for close
-// pairs (Sterbenz), so even pairs 1e-5 Bohr apart next to a nucleus keep a
-// relative error of a few float32 ulps.
+// Near field: mesh points with positions relative to the batch center and
+// two-float field values f = fh + fl and weights w = wh + wl.  The SS
+// difference (fh_j - c_i) + fl_j, with c_i = fh_i, is exact up to one rounding
+// for close pairs (Sterbenz), where f_j - f_i cancels.
 //   Yukawa term  e^{-k r} / r * w_j (f_j - c_i),
 //   Coulomb term (rho_j - c_i e^{-r^2/a^2}) w_j / r.
-template <int NY, bool HH, bool SS, bool SELF>
-__device__ __forceinline__ void tile_near(const float4* __restrict__ srec, const float4* __restrict__ slo,
-                                          const float* __restrict__ sa, const float* __restrict__ sb, int nk,
-                                          const float (&tx)[kTPT], const float (&ty)[kTPT], const float (&tz)[kTPT],
-                                          const float (&lx)[kTPT], const float (&ly)[kTPT], const float (&lz)[kTPT],
-                                          const float (&nc)[kTPT][NY + HH], float (&hi)[kTPT][NY + HH],
-                                          float (&lo)[kTPT][NY + HH], const KParams& kp)
+template <int NY, bool HH, bool SS, bool SELF, int TPT>
+__device__ __forceinline__ void tile_near(const float4* __restrict__ srec, const float4* __restrict__ sv, int nk,
+                                          const float (&tx)[TPT], const float (&ty)[TPT], const float (&tz)[TPT],
+                                          const float (&nc)[TPT][NY + HH], float (&hi)[TPT][NY + HH],
+                                          float (&lo)[TPT][NY + HH], const KParams& kp)
 {
     constexpr int NF = NY + HH;
+    constexpr int G = TileLayout<NF>::G;
     for (int k0 = 0; k0 < nk; k0 += kFold) {
-        float acc[kTPT][NF];
+        float acc[TPT][NF];
 #pragma unroll
-        for (int j = 0; j < kTPT; j++)
+        for (int j = 0; j < TPT; j++)
 #pragma unroll
             for (int o = 0; o < NF; o++) acc[j][o] = 0.0f;
 #pragma unroll 2
         for (int k = k0; k < k0 + kFold; k++) {
             const float4 s = srec[k];
-            const float4 sl = slo[k];
-            float fh[NF], fl[NF];
+            float v[4 * G];
+            load_values<NF>(sv, k, v);
 #pragma unroll
-            for (int o = 0; o < NF; o++) {
-                fh[o] = sa[o * kTile + k];
-                fl[o] = sb[o * kTile + k];
-            }
-#pragma unroll
-            for (int j = 0; j < kTPT; j++) {
-                const float dx = __fadd_rn(__fsub_rn(s.x, tx[j]), __fsub_rn(sl.x, lx[j]));
-                const float dy = __fadd_rn(__fsub_rn(s.y, ty[j]), __fsub_rn(sl.y, ly[j]));
-                const float dz = __fadd_rn(__fsub_rn(s.z, tz[j]), __fsub_rn(sl.z, lz[j]));
+            for (int j = 0; j < TPT; j++) {
+                const float dx = s.x - tx[j], dy = s.y - ty[j], dz = s.z - tz[j];
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 float ri = rsqrt_approx(r2);
                 if (SELF) ri = r2 > 0.0f ? ri : 0.0f;
                 const float r = r2 * ri;
-                const float riw = fmaf(ri, sl.w, ri * s.w);  // ri (w_hi + w_lo)
+                const float riw = fmaf(ri, v[2 * NF], ri * s.w);  // ri (w_hi + w_lo)
 #pragma unroll
                 for (int o = 0; o < NY; o++) {
                     const float e = ex2_approx(kp.ky[o] * r);
-                    const float d = SS ? __fadd_rn(__fadd_rn(fh[o], nc[j][o]), fl[o]) : __fadd_rn(fh[o], fl[o]);
+                    const float d =
+                        SS ? __fadd_rn(__fadd_rn(v[o], nc[j][o]), v[NF + o]) : __fadd_rn(v[o], v[NF + o]);
                     acc[j][o] = fmaf(e * riw, d, acc[j][o]);
                 }
                 if (HH) {
                     float d;
                     if (SS) {
                         const float g = ex2_approx(kp.ga * r2);
-                        d = __fadd_rn(fmaf(nc[j][NY], g, fh[NY]), fl[NY]);
+                        d = __fadd_rn(fmaf(nc[j][NY], g, v[NY]), v[NF + NY]);
                     } else {
-                        d = __fadd_rn(fh[NY], fl[NY]);
+                        d = __fadd_rn(v[NY], v[NF + NY]);
                     }
                     acc[j][NY] = fmaf(riw, d, acc[j][NY]);
                 }
             }
         }
-        fold<NF>(acc, hi, lo);
+        fold<NF, TPT>(acc, hi, lo);
     }
 }
 
-// two-float x = (h, l) plus float64 offset o, renormalised
-__device__ __forceinline__ void add_offset(float h, float l, double o, float& rh, float& rl)
-{
-    const float oh = (float)o;
-    const float ol = (float)(o - (double)oh);
-    float s, e;
-    two_sum(h, oh, s, e);
-    e = __fadd_rn(e, __fadd_rn(l, ol));
-    rh = __fadd_rn(s, e);
-    rl = __fsub_rn(e, __fsub_rn(rh, s));
-}
-
 template <int NY, bool HH, bool SS>
-__global__ void __launch_bounds__(kThreads32) k_interact32(const Item* __restrict__ items,
+__global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item* __restrict__ items,
                                                            const Entry* __restrict__ ents,
                                                            const double* __restrict__ cen,
                                                            const float4* __restrict__ rec4,
@@ -233,28 +241,28 @@ __global__ void __launch_bounds__(kThreads32) k_interact32(const Item* __restric
                                                            double* __restrict__ part, int nf_tot, int field0)
 {
     constexpr int NF = NY + HH;
+    constexpr int G = TileLayout<NF>::G;
+    constexpr int TPT = Tpt<NF>::value;
+    constexpr int THREADS = Tpt<NF>::threads;
     __shared__ float4 srec[kTile];
-    __shared__ float4 slo[kTile];
-    __shared__ float sa[NF * kTile];
-    __shared__ float sb[NF * kTile];
+    __shared__ float4 sv[G * kTile];
 
     const Item it = items[blockIdx.x];
     const int tid = threadIdx.x;
-    float tx[kTPT], ty[kTPT], tz[kTPT], lx[kTPT], ly[kTPT], lz[kTPT];
-    float nc[kTPT][NF];
-    float hi[kTPT][NF], lo[kTPT][NF];
+    float tx[TPT], ty[TPT], tz[TPT];
+    float nc[TPT][NF];
+    float hi[TPT][NF], lo[TPT][NF];
 #pragma unroll
-    for (int j = 0; j < kTPT; j++) {
-        const int p = it.t0 + tid + j * kThreads32;
+    for (int j = 0; j < TPT; j++) {
+        const int p = it.t0 + tid + j * THREADS;
         const bool ok = p < it.t1;
         const float4 r = ok ? rec4[p] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 rl = ok ? rec4lo[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-        tx[j] = r.x;
-        ty[j] = r.y;
-        tz[j] = r.z;
-        lx[j] = rl.x;
-        ly[j] = rl.y;
-        lz[j] = rl.z;
+        // rounded exactly as a staged source of the batch's own leaf, so the
+        // self pair gives r = 0 bit for bit
+        tx[j] = (float)(((double)r.x + (double)rl.x) + 0.0);
+        ty[j] = (float)(((double)r.y + (double)rl.y) + 0.0);
+        tz[j] = (float)(((double)r.z + (double)rl.z) + 0.0);
 #pragma unroll
         for (int o = 0; o < NF; o++) {
             nc[j][o] = ok ? -fa[o * lda + p] : 0.0f;  // SS constant c_i = fh_i
@@ -274,8 +282,11 @@ __global__ void __launch_bounds__(kThreads32) k_interact32(const Item* __restric
             const int nk = (ns + 7) & ~7;
             __syncthreads();
 #pragma unroll
-            for (int h = 0; h < kTile / kThreads32; h++) {
-                const int k = tid + h * kThreads32;
+            for (int h = 0; h < kTile / THREADS; h++) {
+                const int k = tid + h * THREADS;
+                float v[4 * G];
+#pragma unroll
+                for (int m = 0; m < 4 * G; m++) v[m] = 0.0f;
                 if (k < ns) {
                     float4 r = rec4[s0 + k];
                     if (far) {
@@ -284,41 +295,41 @@ __global__ void __launch_bounds__(kThreads32) k_interact32(const Item* __restric
                         r.y = (float)((double)r.y + oy);
                         r.z = (float)((double)r.z + oz);
                     } else {
+                        // point = leaf center + (delta_hi + delta_lo); one rounding
                         const float4 rl = rec4lo[s0 + k];
-                        float4 l;
-                        add_offset(r.x, rl.x, ox, r.x, l.x);
-                        add_offset(r.y, rl.y, oy, r.y, l.y);
-                        add_offset(r.z, rl.z, oz, r.z, l.z);
-                        l.w = rl.w;  // low part of the weight
-                        slo[k] = l;
+                        r.x = (float)(((double)r.x + (double)rl.x) + ox);
+                        r.y = (float)(((double)r.y + (double)rl.y) + oy);
+                        r.z = (float)(((double)r.z + (double)rl.z) + oz);
+                        v[2 * NF] = rl.w;  // low part of the weight
 #pragma unroll
-                        for (int o = 0; o < NF; o++) sb[o * kTile + k] = fb[o * ldb + s0 + k];
+                        for (int o = 0; o < NF; o++) v[NF + o] = fb[o * ldb + s0 + k];
                     }
                     srec[k] = r;
 #pragma unroll
-                    for (int o = 0; o < NF; o++) sa[o * kTile + k] = fa[o * lda + s0 + k];
+                    for (int o = 0; o < NF; o++) v[o] = fa[o * lda + s0 + k];
                 } else if (k < nk) {
                     // padding record: far away, zero weight and values -> contributes 0
                     srec[k] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-                    slo[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int o = 0; o < NF; o++) sa[o * kTile + k] = sb[o * kTile + k] = 0.0f;
                 }
+                if (k < nk)
+#pragma unroll
+                    for (int g = 0; g < G; g++)
+                        sv[g * kTile + k] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
             }
             __syncthreads();
             if (far)
-                tile_far<NY, HH, SS>(srec, sa, nk, tx, ty, tz, nc, hi, lo, kp);
+                tile_far<NY, HH, SS, TPT>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
             else if (self)
-                tile_near<NY, HH, SS, true>(srec, slo, sa, sb, nk, tx, ty, tz, lx, ly, lz, nc, hi, lo, kp);
+                tile_near<NY, HH, SS, true, TPT>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
             else
-                tile_near<NY, HH, SS, false>(srec, slo, sa, sb, nk, tx, ty, tz, lx, ly, lz, nc, hi, lo, kp);
+                tile_near<NY, HH, SS, false, TPT>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
         }
     }
     double* out = part + ((size_t)blockIdx.x * nf_tot + field0) * kTargetsPerItem;
 #pragma unroll
-    for (int j = 0; j < kTPT; j++)
+    for (int j = 0; j < TPT; j++)
 #pragma unroll
-        for (int o = 0; o < NF; o++) out[o * kTargetsPerItem + tid + j * kThreads32] = (double)hi[j][o] + (double)lo[j][o];
+        for (int o = 0; o < NF; o++) out[o * kTargetsPerItem + tid + j * THREADS] = (double)hi[j][o] + (double)lo[j][o];
 }
 
 // ---------------------------------------------------------------- bias calibration
@@ -435,12 +446,12 @@ void launch32_ss(Tree& T, bool ss, const KParams& kp, const float* q, const floa
     const int grid = (int)T.nitems;
     cudaStream_t s = T.stream;
     if (ss)
-        launch(k_interact32<NY, HH, true>, grid, kThreads32, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
+        launch(k_interact32<NY, HH, true>, grid, Tpt<NY + HH>::threads, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
                                                                T.cl_cen.as<double>(), T.rec4.as<float4>(),
                                                                T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kp, part,
                                                                nf_tot, field0);
     else
-        launch(k_interact32<NY, HH, false>, grid, kThreads32, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
+        launch(k_interact32<NY, HH, false>, grid, Tpt<NY + HH>::threads, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
                                                                 T.cl_cen.as<double>(), T.rec4.as<float4>(),
                                                                 T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kp, part,
                                                                 nf_tot, field0);

@@ -33,14 +33,17 @@ struct Error : std::runtime_error {
         if (!(cond)) throw ::tagi::Error(TAGI_ERR_INVALID_ARG, std::string(msg)); \
     } while (0)
 
-// Device buffer owned by a tree; freed by the tree destructor.
+// Device buffer from the caching allocator (alloc.cu); released to the cache
+// of the stream it was allocated for when destroyed or regrown.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    int dev = 0;
+    cudaStream_t stream = nullptr;
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes)
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), dev(o.dev), stream(o.stream)
     {
         o.p = nullptr;
         o.bytes = 0;
@@ -51,6 +54,8 @@ struct DevBuf {
             release();
             p = o.p;
             bytes = o.bytes;
+            dev = o.dev;
+            stream = o.stream;
             o.p = nullptr;
             o.bytes = 0;
         }
@@ -62,6 +67,14 @@ struct DevBuf {
     template <class T>
     T* as() const { return static_cast<T*>(p); }
 };
+
+// Allocations made while an AllocStream is alive are ordered on its stream.
+struct AllocStream {
+    cudaStream_t prev;
+    explicit AllocStream(cudaStream_t s);
+    ~AllocStream();
+};
+void trim_cache();  // synchronises the device and frees every cached block
 
 // Every kernel of the library is launched through launch(), which counts it
 // (tagi_kernel_launches) before the <<<>>> launch.

@@ -195,35 +195,50 @@ __global__ void k_blkcount(const signed char* __restrict__ code, int64_t n, int6
     }
 }
 
-// prefix_b(x): positions < x with code b, plus a bin offset that cancels.
-__device__ int64_t prefix_at(const int64_t* off, const signed char* code, int64_t nblk, int b, int64_t x)
+// One warp per cluster of the level: per-bin counts between begin and end and
+// the bin prefix at begin (block offsets plus a warp-parallel partial count).
+__device__ void prefix8(const int64_t* off, const signed char* code, int64_t nblk, int64_t x, int lane, int64_t (&pf)[8])
 {
-    int64_t blk = x / kBlk;
-    int64_t s = off[b * nblk + blk];
-    for (int64_t q = blk * kBlk; q < x; q++) s += (code[q] == b);
-    return s;
+    const int64_t blk = x / kBlk;
+    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t q = blk * kBlk + lane; q < x; q += 32) {
+        const int k = code[q];
+#pragma unroll
+        for (int b = 0; b < 8; b++) cnt[b] += (k == b);
+    }
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        int v = cnt[b];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        pf[b] = off[b * nblk + blk] + v;
+    }
 }
 
 __global__ void k_counts(int first, int last, const int* begin, const int* end, const int* smask,
                          const signed char* code, const int64_t* off, int64_t nblk, int* cnt, int64_t* pfx,
                          int64_t* nnz)
 {
-    int c = first + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= last) return;
-    int j = c - first;
-    int z = 0;
-    for (int b = 0; b < 8; b++) {
-        int v = 0;
-        int64_t pb = 0;
-        if (smask[c]) {
-            pb = prefix_at(off, code, nblk, b, begin[c]);
-            v = (int)(prefix_at(off, code, nblk, b, end[c]) - pb);
-        }
-        cnt[8 * j + b] = v;
-        pfx[8 * j + b] = pb;
-        z += v > 0;
+    const int c = first + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32);
+    const int lane = threadIdx.x & 31;
+    if (c >= last) return;  // uniform per warp
+    const int j = c - first;
+    int64_t pb[8], pe[8];
+    if (smask[c]) {
+        prefix8(off, code, nblk, begin[c], lane, pb);
+        prefix8(off, code, nblk, end[c], lane, pe);
+    } else {
+        for (int b = 0; b < 8; b++) pb[b] = pe[b] = 0;
     }
-    nnz[j] = z;
+    if (lane == 0) {
+        int z = 0;
+        for (int b = 0; b < 8; b++) {
+            const int v = (int)(pe[b] - pb[b]);
+            cnt[8 * j + b] = v;
+            pfx[8 * j + b] = pb[b];
+            z += v > 0;
+        }
+        nnz[j] = z;
+    }
 }
 
 __global__ void k_children(int first, int last, int nc0, const int64_t* cbase, const int* begin, const int* cnt,
@@ -476,13 +491,14 @@ __global__ void k_item_fill(int nleaf, const int* leaves, const int* begin, cons
                             const Entry* ent, int seg_src, const int64_t* chunk_off, const int64_t* item_off,
                             Item* items, int* tc_item0, int* tc_t0, int* tc_t1, int* tc_batch)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    // one block per leaf, one thread per target chunk of the leaf
+    const int j = blockIdx.x;
     if (j >= nleaf) return;
     int b = leaves[j];
     int nb = end[b] - begin[b];
     int ch = (int)(chunk_off[j + 1] - chunk_off[j]);
     int segs = ch ? (int)((item_off[j + 1] - item_off[j]) / ch) : 0;
-    for (int ci = 0; ci < ch; ci++) {
+    for (int ci = threadIdx.x; ci < ch; ci += blockDim.x) {
         int64_t tc = chunk_off[j] + ci;
         int t0 = begin[b] + ci * kTargetsPerItem;
         int t1 = min(begin[b] + nb, t0 + kTargetsPerItem);
@@ -598,10 +614,14 @@ __global__ void k_check_finite(const double* a, int64_t n, int* bad)
 inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 struct Host1 {
-    // pinned scalar for readbacks
+    // pinned scalars for readbacks, allocated once per host thread
     int64_t* h = nullptr;
-    Host1() { TAGI_CUDA(cudaMallocHost(&h, 8 * sizeof(int64_t))); }
-    ~Host1() { cudaFreeHost(h); }
+    Host1()
+    {
+        thread_local int64_t* buf = nullptr;
+        if (!buf) TAGI_CUDA(cudaMallocHost(&buf, 8 * sizeof(int64_t)));
+        h = buf;
+    }
 };
 
 }  // namespace
@@ -734,7 +754,7 @@ void build_tree(Tree& T, const double* xyz, const double* w)
         cbase.ensure(8 * ((size_t)nl + 1));
         bfirst.ensure(32 * (size_t)nl);
         bid.ensure(32 * (size_t)nl);
-        launch(k_counts, nblocks(nl, 128), 128, 0, s, first, last, T.cl_begin.as<int>(), T.cl_end.as<int>(),
+        launch(k_counts, nblocks(32 * (int64_t)nl, 128), 128, 0, s, first, last, T.cl_begin.as<int>(), T.cl_end.as<int>(),
                                                    smask.as<int>(), code.as<signed char>(), boff.as<int64_t>(), nblk,
                                                    cnt.as<int>(), pfx.as<int64_t>(), nnz.as<int64_t>());
         exclusive_scan_i64(nnz.as<int64_t>(), cbase.as<int64_t>(), nl, s);
@@ -863,7 +883,7 @@ void build_tree(Tree& T, const double* xyz, const double* w)
     TAGI_LAUNCH_CHECK();
 
     // ---- work items of the near/far kernel
-    const int seg_src = 32768;
+    const int seg_src = 8192;
     DevBuf nch, nit, choff, itoff;
     nch.ensure(8 * (size_t)nleaf);
     nit.ensure(8 * (size_t)nleaf);
@@ -882,7 +902,7 @@ void build_tree(Tree& T, const double* xyz, const double* w)
     T.tc_t0.ensure(4 * (size_t)T.ntchunk);
     T.tc_t1.ensure(4 * (size_t)T.ntchunk);
     T.tc_batch.ensure(4 * (size_t)T.ntchunk);
-    launch(k_item_fill, nblocks(nleaf, 128), 128, 0, s, nleaf, T.leaves.as<int>(), T.cl_begin.as<int>(),
+    launch(k_item_fill, nleaf, 32, 0, s, nleaf, T.leaves.as<int>(), T.cl_begin.as<int>(),
                                                     T.cl_end.as<int>(), T.ent_off.as<int64_t>(), T.ent.as<Entry>(),
                                                     seg_src, choff.as<int64_t>(), itoff.as<int64_t>(),
                                                     T.items.as<Item>(), T.tc_item0.as<int>(), T.tc_t0.as<int>(),
