@@ -214,6 +214,23 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ ranks
+def combine_ranks(ms, interactions, world, device):
+    """Replicas: every rank times its own workload.  Returns the slowest
+    rank's step time and the interactions of all ranks together (the
+    whole-job rate is their ratio).  Uses whatever process group is open."""
+    if world <= 1:
+        return float(ms), float(interactions)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot = torch.tensor([float(interactions)], dtype=torch.float64, device=device)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(tot.item())
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -292,16 +309,7 @@ def main():
     ms = float(np.mean(times))
     nf = nw + 1
     inter = (info["near_pairs"] + info["far_pairs"]) * nf
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-        tot = torch.tensor([float(inter)], device=dev)
-        torch.distributed.all_reduce(tot)
-        inter_all = float(tot.item())
-    else:
-        inter_all = float(inter)
+    t_max, inter_all = combine_ranks(ms, inter, world, dev)
     value = inter_all / (t_max * 1e-3)
 
     # ---- end to end through the public API: pinned host inputs -> device,
