@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--impl", default="tagi", choices=["tagi", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain-form comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="li", choices=["li", "li-small"],
+                    help="li: the benchmark workload (309k points); li-small: tol_m 1e-3 mesh (99k) for profiling")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="build one tree and run two Green steps, nothing timed (for ncu captures)")
     return ap.parse_args()
 
 
@@ -54,10 +58,30 @@ def dist_info():
     return rank, world, local
 
 
+WORKLOAD = "li"
+
+
 def make_workload(seed):
     from paper_2003_01833_gb300 import workloads as W
 
-    return W.lithium(seed=seed)
+    return W.lithium(seed=seed, tol_m=1e-3) if WORKLOAD == "li-small" else W.lithium(seed=seed)
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of k_interact32 on the benchmark workload, from
+    the ncu capture summarised in profiles/, if that capture was taken on the
+    current source of the kernel (else None)."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2003_01833_gb300", "csrc", "interact.cu")
+    rec = os.path.join(ROOT, "profiles", "k_interact32_li309k_traffic.txt")
+    if not os.path.exists(rec):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    vals = dict(line.split()[:2] for line in open(rec) if line.strip() and not line.startswith("#"))
+    if vals.get("interact_cu_sha256") != digest:
+        return None
+    return float(vals["dram_bytes_per_launch"])
 
 
 # ------------------------------------------------------------------ clocks
@@ -232,8 +256,69 @@ def combine_ranks(ms, interactions, world, device):
 
 
 # ------------------------------------------------------------------ GPU arm
+def graph_replay(T, args, wl, xyz, w, params, veff, rho, vh, psi0, flush, inter, dev):
+    """Time whole Green iterations replayed from a captured CUDA graph on a
+    tree built once.  Capture needs a created stream, so this runs on one."""
+    import torch
+
+    nw = wl.psi.shape[0]
+    side = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(side):
+        h = T.tagi_tree_build(xyz, w, params)
+        psi_g = psi0.clone()
+        eps_g = torch.tensor(wl.eps, device=dev)
+        res_g = torch.empty(nw, dtype=torch.float64, device=dev)
+        eh_g = torch.empty(1, dtype=torch.float64, device=dev)
+        g = T.tagi_green_graph_create(h, veff, wl.vshift, psi_g, eps_g, res_g, rho=rho, vh=vh, eh=eh_g)
+        eps0 = eps_g.clone()
+        times = []
+        for i in range(args.warmup + args.steps):
+            # the same first iteration every time (the synthetic start is not
+            # an eigenstate; repeated iterations would walk away from it)
+            psi_g.copy_(psi0)
+            eps_g.copy_(eps0)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(side)
+            T.tagi_green_graph_launch(g)
+            e1.record(side)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        T.tagi_green_graph_check(g)
+        T.tagi_green_graph_destroy(g)
+        T.tagi_tree_destroy(h)
+    ms = float(np.mean(times))
+    return {"ms_per_green_iteration": ms, "interactions_per_s": inter / (ms * 1e-3),
+            "note": "tree built once; each replay is one whole Green iteration (a3-a8) from a CUDA graph"}
+
+
+def profile_case(args):
+    """One tree and two Green steps, nothing else: the command ncu wraps."""
+    import torch
+
+    import paper_2003_01833_gb300.tagi as T
+
+    wl = make_workload(1)
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.tensor(a, device=dev)
+    with T.Tree(t(wl.mesh.xyz), t(wl.mesh.w), theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size,
+                prec=T.TAGI_FP32C) as tr:
+        vh = torch.empty(wl.n, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            psi = t(wl.psi)
+            eps, res, eh = T.tagi_green_step(tr.handle, t(wl.veff), wl.vshift, psi, wl.eps, rho=t(wl.rho), vh=vh)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": WORKLOAD, "n": wl.n, "eps": [float(x) for x in eps]}))
+
+
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = args.workload
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -311,6 +396,9 @@ def main():
     inter = (info["near_pairs"] + info["far_pairs"]) * nf
     t_max, inter_all = combine_ranks(ms, inter, world, dev)
     value = inter_all / (t_max * 1e-3)
+
+    # ---- Green iterations replayed from a captured CUDA graph (fixed tree)
+    graph = graph_replay(T, args, wl, xyz, w, params, veff, rho, vh, psi0, flush, inter, dev) if rank == 0 else None
 
     # ---- end to end through the public API: pinned host inputs -> device,
     # step, results -> host, all inside the timed region
@@ -392,7 +480,7 @@ def main():
         "s_per_green_iteration": t_max * 1e-3,
         "phases_ms_per_step": {g: prof[g][0] / max(1, args.steps) for g in prof},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "interactions/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": kernel_traffic(),
                      "kernel": "k_interact32 (near/far)", "issue_per_interaction": per_inter,
                      "peak_model": f"{sms} SMs x 128 issue/clk x {clk_mhz:.0f} MHz / {per_inter:.2f} instr per "
                                    "interaction (measured clock)"},
@@ -400,6 +488,7 @@ def main():
         "e2e": {"value": inter_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "s_per_step": e2e_s},
         "gpu_launches": launches,
+        "graph_replay": graph,
         "plain_fp64": plain,
         "cpu_baseline": cpu,
     }

@@ -220,6 +220,31 @@ tagi_status tagi_profile_read(int group, double* ms, int64_t* count);
 tagi_status tagi_yukawa_direct_noalloc(const double* xyz, const double* w, const double* f, const double* k,
                                        int nf, int64_t n, double* u, void* stream);
 
+/* A whole Green iteration (tagi_green_step's computation) captured as a CUDA
+ * graph, for loops of Green iterations on a fixed tree (FP32C only).  Every
+ * per-iteration value lives in device memory, so a replay reads the current
+ * eigenvalues, updates the orbitals and eigenvalues in place, and writes the
+ * residuals (and E_H) without any host synchronisation.
+ *   create: veff [dev] n; psi [dev] nw*n, in/out on every replay; eps [dev]
+ *     nw, unshifted, in/out; rho [dev] n or NULL; vh [dev] n (with rho);
+ *     resid [dev] nw, out; eh [dev] 1, out (with rho).  1 <= nw < 128.
+ *     Runs one eager iteration on private copies of psi and eps (sizing every
+ *     buffer, checking eps + vshift < 0), then captures the sequence on
+ *     `stream`, which must be a created stream (not NULL or a default stream).  The pointers are baked into the graph: keep the buffers and
+ *     the tree alive until the graph is destroyed, and do not call other
+ *     entry points on the same tree while replays are in flight.
+ *   launch: enqueue one Green iteration on `stream` (asynchronous).
+ *   check: synchronise `stream` and report TAGI_ERR_INVALID_ARG if a replay
+ *     met eps + vshift >= 0 (Section 3.3).
+ *   destroy: waits for the device; NULL is accepted. */
+typedef struct tagi_green_graph tagi_green_graph;
+tagi_status tagi_green_graph_create(tagi_tree* tree, const double* veff, double vshift, double* psi, double* eps,
+                                    int nw, const double* rho, double* vh, double* resid, double* eh, void* stream,
+                                    tagi_green_graph** out);
+tagi_status tagi_green_graph_launch(tagi_green_graph* graph, void* stream);
+tagi_status tagi_green_graph_check(tagi_green_graph* graph, void* stream);
+tagi_status tagi_green_graph_destroy(tagi_green_graph* graph);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* tagi_last_error(void);
 

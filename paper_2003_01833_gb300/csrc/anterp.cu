@@ -22,30 +22,28 @@ constexpr int kAntThreads = 256;
 constexpr int kAntTile = 64;
 constexpr int kMaxPPT = 4;  // proxies per thread: (9+1)^3 = 1000 <= 4 * 256
 
-// Barycentric Lagrange basis at t in [-1, 1] on the nodes cos(pi k / n).
-// A coordinate equal to a node takes the Kronecker delta; h == 0 (zero
-// extent) puts all weight on node 0.
-template <class R>
-__device__ void basis(R t, bool degenerate, int n, const R* nodes, R* L)
+// Lagrange basis at t in [-1, 1] on the nodes cos(pi k / n) (Eq. Lagrange_polynomials).
+// Division-free (first barycentric form):
+//   L_k(t) = prod_{j != k} (t - s_j) * inv_k,  inv_k = 1 / prod_{j != k} (s_k - s_j),
+// with prefix and suffix products; exact zeros at the other nodes.  float64
+// divisions are slow on this GPU, and this form needs none per point.
+__device__ __forceinline__ void basis_prod(double t, bool degenerate, int n, const double* s, const double* inv,
+                                           double* L)
 {
     if (degenerate) {
-        for (int k = 0; k <= n; k++) L[k] = k == 0 ? R(1) : R(0);
+        for (int k = 0; k <= n; k++) L[k] = k == 0 ? 1.0 : 0.0;
         return;
     }
-    R den = 0;
-    int hit = -1;
+    double pre = 1.0;
     for (int k = 0; k <= n; k++) {
-        R diff = t - nodes[k];
-        if (diff == R(0)) hit = k;
-        R b = ((k & 1) ? R(-1) : R(1)) * ((k == 0 || k == n) ? R(0.5) : R(1));
-        L[k] = b / diff;
-        den += L[k];
+        L[k] = pre;
+        pre *= t - s[k];
     }
-    if (hit >= 0) {
-        for (int k = 0; k <= n; k++) L[k] = k == hit ? R(1) : R(0);
-        return;
+    double suf = 1.0;
+    for (int k = n; k >= 0; k--) {
+        L[k] *= suf * inv[k];
+        suf *= t - s[k];
     }
-    for (int k = 0; k <= n; k++) L[k] /= den;
 }
 
 // R: arithmetic type of the basis and per-tile sums; A: accumulator type.
@@ -62,15 +60,26 @@ __global__ void __launch_bounds__(kAntThreads) k_ant(const AntItem* __restrict__
     const AntItem it = items[blockIdx.x];
     const int m = degree + 1, P = m * m * m;
     const int c = it.cluster;
-    double cc[3], hh[3];
+    double cc[3], hh[3], ih[3];
     for (int d = 0; d < 3; d++) {
         cc[d] = (lo[3 * c + d] + hi[3 * c + d]) * 0.5;
         hh[d] = (hi[3 * c + d] - lo[3 * c + d]) * 0.5;
+        ih[d] = hh[d] == 0.0 ? 0.0 : 1.0 / hh[d];
     }
-    if (threadIdx.x <= degree) {
+    __shared__ double dnodes[kMaxDegree + 1], inv[kMaxDegree + 1];
+    if (threadIdx.x == 0) {
         // FP32C proxies sit on the float32-rounded nodes; interpolate there
-        const double sk = cos(M_PI * threadIdx.x / degree);
-        nodes[threadIdx.x] = f32nodes ? (R)(float)sk : (R)sk;
+        for (int k = 0; k <= degree; k++) {
+            const double sk = cos(M_PI * k / degree);
+            nodes[k] = f32nodes ? (R)(float)sk : (R)sk;
+            dnodes[k] = (double)nodes[k];
+        }
+        for (int k = 0; k <= degree; k++) {
+            double d = 1.0;
+            for (int j = 0; j <= degree; j++)
+                if (j != k) d *= dnodes[k] - dnodes[j];
+            inv[k] = 1.0 / d;
+        }
     }
     int k1[kMaxPPT], k2[kMaxPPT], k3[kMaxPPT];
     A acc[kMaxPPT][NQ];
@@ -92,15 +101,14 @@ __global__ void __launch_bounds__(kAntThreads) k_ant(const AntItem* __restrict__
             if (j < nt) {
                 const double* x = d == 0 ? px : (d == 1 ? py : pz);
                 bool deg = hh[d] == 0.0;
-                // scale-invariant barycentric form on [-1, 1], evaluated in
+                // the basis on [-1, 1], evaluated in
                 // float64 for both paths (a float32 evaluation is biased at
                 // the 1e-8 level, which the singularity subtraction would
                 // amplify); the float32 path interpolates on the float32
                 // nodes, where its proxies sit
-                double nd[kMaxDegree + 1], Ld[kMaxDegree + 1];
-                for (int q = 0; q <= degree; q++) nd[q] = (double)nodes[q];
-                const double td = deg ? 0.0 : (x[p0 + j] - cc[d]) / hh[d];
-                basis<double>(td, deg, degree, nd, Ld);
+                double Ld[kMaxDegree + 1];
+                const double td = deg ? 0.0 : (x[p0 + j] - cc[d]) * ih[d];
+                basis_prod(td, deg, degree, dnodes, inv, Ld);
                 for (int q = 0; q <= degree; q++) L[q] = (R)Ld[q];
             } else {
                 for (int k = 0; k <= degree; k++) L[k] = R(0);

@@ -14,7 +14,6 @@
 
 namespace tagi {
 
-void form_fields(Tree& T, const double* veff, double vshift, const double* psi, int nw, double* f);
 
 namespace {
 std::atomic<int64_t> g_launches{0};
@@ -33,6 +32,8 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 ProfScope::ProfScope(int g, cudaStream_t s) : group(g), stream(s)
 {
     if (!g_prof_on.load()) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
         a = b = nullptr;
         return;
@@ -105,10 +106,14 @@ void ensure_part(Tree& T, int nf)
     T.part.ensure(sizeof(double) * (size_t)T.nitems * nf * kTargetsPerItem);
 }
 
-// Convolutions of nf caller-order rows f (device) with kinds/kval; outputs out[o].
-void run_convolution(Tree& T, const double* f, int nf, const int* kinds, const double* kval, double* const* out)
+// Convolutions of nf caller-order rows f (device): rates from R (and eps_dev
+// for the first R.n_eps fields), outputs out[o].  Enqueued on T.stream, no
+// host synchronisation.
+void run_convolution(Tree& T, const double* f, const RateSrc& R, const double* eps_dev, double* const* out)
 {
+    const int nf = R.nf;
     ensure_part(T, nf);
+    make_rates(T, R, eps_dev);
     if (T.prec == TAGI_FP32C) {
         {
             ProfScope ps(kProfAnterp, T.stream);
@@ -116,7 +121,7 @@ void run_convolution(Tree& T, const double* f, int nf, const int* kinds, const d
             anterpolate_fields32(T, nf);
         }
         ProfScope ps(kProfInteract, T.stream);
-        interact32(T, nf, kinds, kval, T.part.as<double>());
+        interact32(T, nf, R.kind, T.rates32.as<float>(), T.part.as<double>());
     } else {
         {
             ProfScope ps(kProfAnterp, T.stream);
@@ -125,12 +130,71 @@ void run_convolution(Tree& T, const double* f, int nf, const int* kinds, const d
         }
         ProfScope ps(kProfInteract, T.stream);
         for (int o = 0; o < nf; o++)
-            interact64(T, o, nf, kinds[o], kval[o], T.q64.as<double>() + (size_t)o * T.nrec,
+            interact64(T, o, nf, R.kind[o], T.rates64.as<double>(), T.q64.as<double>() + (size_t)o * T.nrec,
                        T.c64.as<double>() + (size_t)o * T.n, T.part.as<double>());
     }
     ProfScope ps(kProfEpilogue, T.stream);
-    reduce_epilogue(T, nf, kinds, kval, T.part.as<double>(), out);
+    reduce_epilogue(T, nf, R.kind, T.part.as<double>(), out);
 }
+
+RateSrc host_rates(const Tree& T, int nf)
+{
+    TAGI_REQUIRE(nf >= 1 && nf <= kMaxCallFields, "at most 128 fields per call");
+    RateSrc R{};
+    R.nf = nf;
+    R.fp32 = T.prec == TAGI_FP32C;
+    return R;
+}
+
+void clear_err(Tree& T)
+{
+    T.errflag.ensure(16);
+    TAGI_CUDA(cudaMemsetAsync(T.errflag.p, 0, 4, T.stream));
+}
+
+int read_err(Tree& T)
+{
+    int h = 0;
+    TAGI_CUDA(cudaMemcpyAsync(&h, T.errflag.p, 4, cudaMemcpyDeviceToHost, T.stream));
+    TAGI_CUDA(cudaStreamSynchronize(T.stream));
+    return h;
+}
+
+// One Green iteration with every per-iteration value on the device (eps_dev,
+// resid_dev, eh_dev): the sequence a captured graph replays.
+void green_step_device(Tree& T, const double* veff, double vshift, double* psi, double* eps_dev, int nw,
+                       const double* rho, double* vh, double* resid_dev, double* eh_dev)
+{
+    const int64_t n = T.n;
+    const int nf = nw + (rho ? 1 : 0);
+    TAGI_REQUIRE(nf <= kMaxCallFields, "at most 127 orbitals per Green step");
+    T.fbuf.ensure(sizeof(double) * (size_t)nf * n);
+    T.ubuf.ensure(sizeof(double) * (size_t)nw * n);
+    double* f = T.fbuf.as<double>();
+    form_fields(T, veff, vshift, psi, nw, f);
+    if (rho)
+        TAGI_CUDA(cudaMemcpyAsync(f + (size_t)nw * n, rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, T.stream));
+    RateSrc R = host_rates(T, nf);
+    R.n_eps = nw;
+    R.vshift = vshift;
+    std::vector<double*> out(nf);
+    for (int o = 0; o < nw; o++) out[o] = T.ubuf.as<double>() + (size_t)o * n;
+    if (rho) {
+        R.kind[nw] = 1;
+        R.val[nw] = T.alpha;
+        out[nw] = vh;
+    }
+    run_convolution(T, f, R, eps_dev, out.data());
+    ProfScope ps(kProfReduce, T.stream);
+    green_reductions(T, f, psi, T.ubuf.as<double>(), nw, eps_dev, resid_dev);
+    if (rho && eh_dev) hartree_energy(T, vh, rho, eh_dev);
+}
+
+struct GreenGraph {
+    Tree* T = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+};
 
 }  // namespace
 }  // namespace tagi
@@ -322,11 +386,12 @@ tagi_status tagi_yukawa_conv(tagi_tree* tree, const double* f, const double* k, 
         for (int o = 0; o < nf; o++) TAGI_REQUIRE(std::isfinite(k[o]) && k[o] > 0.0, "every k must be finite and > 0");
         T->stream = (cudaStream_t)stream;
         AllocStream as(T->stream);
-        std::vector<int> kinds(nf, 0);
-        std::vector<double> kv(k, k + nf);
+        RateSrc R = host_rates(*T, nf);
+        for (int o = 0; o < nf; o++) R.val[o] = k[o];
         std::vector<double*> out(nf);
         for (int o = 0; o < nf; o++) out[o] = u + (size_t)o * T->n;
-        run_convolution(*T, f, nf, kinds.data(), kv.data(), out.data());
+        clear_err(*T);
+        run_convolution(*T, f, R, nullptr, out.data());
     });
 }
 
@@ -337,10 +402,12 @@ tagi_status tagi_coulomb_conv(tagi_tree* tree, const double* rho, double* vh, vo
         TAGI_REQUIRE(rho != nullptr && vh != nullptr, "rho or vh is NULL");
         T->stream = (cudaStream_t)stream;
         AllocStream as(T->stream);
-        int kind = 1;
-        double a = T->alpha;
+        RateSrc R = host_rates(*T, 1);
+        R.kind[0] = 1;
+        R.val[0] = T->alpha;
         double* out = vh;
-        run_convolution(*T, rho, 1, &kind, &a, &out);
+        clear_err(*T);
+        run_convolution(*T, rho, R, nullptr, &out);
     });
 }
 
@@ -353,40 +420,134 @@ tagi_status tagi_green_step(tagi_tree* tree, const double* veff, double vshift, 
         TAGI_REQUIRE(nw >= 1, "nw must be >= 1");
         TAGI_REQUIRE(std::isfinite(vshift), "vshift must be finite");
         TAGI_REQUIRE(rho == nullptr || vh != nullptr, "vh is required when rho is given");
-        std::vector<double> es(nw);
         for (int o = 0; o < nw; o++) {
-            es[o] = eps[o] + vshift;
-            TAGI_REQUIRE(std::isfinite(es[o]) && es[o] < 0.0, "eps + vshift must be negative (Section 3.3)");
+            const double es = eps[o] + vshift;
+            TAGI_REQUIRE(std::isfinite(es) && es < 0.0, "eps + vshift must be negative (Section 3.3)");
         }
         T->stream = (cudaStream_t)stream;
         AllocStream as(T->stream);
+        T->epsd.ensure(sizeof(double) * nw);
+        T->residd.ensure(sizeof(double) * nw);
+        T->ehd.ensure(sizeof(double) * 2);
+        TAGI_CUDA(cudaMemcpyAsync(T->epsd.p, eps, sizeof(double) * nw, cudaMemcpyHostToDevice, T->stream));
+        clear_err(*T);
+        green_step_device(*T, veff, vshift, psi, T->epsd.as<double>(), nw, rho, vh, T->residd.as<double>(),
+                          rho ? T->ehd.as<double>() : nullptr);
+        std::vector<double> r(nw), e(nw);
+        double h = 0.0;
+        TAGI_CUDA(cudaMemcpyAsync(e.data(), T->epsd.p, sizeof(double) * nw, cudaMemcpyDeviceToHost, T->stream));
+        TAGI_CUDA(cudaMemcpyAsync(r.data(), T->residd.p, sizeof(double) * nw, cudaMemcpyDeviceToHost, T->stream));
+        if (rho) TAGI_CUDA(cudaMemcpyAsync(&h, T->ehd.p, sizeof(double), cudaMemcpyDeviceToHost, T->stream));
+        TAGI_REQUIRE(read_err(*T) == 0, "eps + vshift must be negative (Section 3.3)");
+        for (int o = 0; o < nw; o++) eps[o] = e[o];
+        if (resid)
+            for (int o = 0; o < nw; o++) resid[o] = r[o];
+        if (rho && eh) *eh = h;
+    });
+}
+
+tagi_status tagi_green_graph_create(tagi_tree* tree, const double* veff, double vshift, double* psi, double* eps,
+                                    int nw, const double* rho, double* vh, double* resid, double* eh, void* stream,
+                                    tagi_green_graph** out)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    bool capturing = false;
+    cudaGraph_t g = nullptr;
+    try {
+        report_error(TAGI_OK, "");
+        TAGI_REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        Tree* T = as_tree(tree);
+        TAGI_REQUIRE(T->prec == TAGI_FP32C, "graph capture serves the FP32C form (the plain form runs eagerly)");
+        TAGI_REQUIRE(s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread,
+                     "capture needs a created stream (the default streams cannot be captured)");
+        TAGI_REQUIRE(veff && psi && eps && resid, "veff, psi, eps or resid is NULL");
+        TAGI_REQUIRE(nw >= 1 && nw < kMaxCallFields, "need 1 <= nw < 128");
+        TAGI_REQUIRE(std::isfinite(vshift), "vshift must be finite");
+        TAGI_REQUIRE(rho == nullptr || (vh != nullptr && eh != nullptr), "vh and eh are required when rho is given");
+        T->stream = s;
+        AllocStream as(s);
         const int64_t n = T->n;
-        const int nf = nw + (rho ? 1 : 0);
-        T->fbuf.ensure(sizeof(double) * (size_t)nf * n);
-        T->ubuf.ensure(sizeof(double) * (size_t)nw * n);
-        double* f = T->fbuf.as<double>();
-        form_fields(*T, veff, vshift, psi, nw, f);
-        if (rho)
-            TAGI_CUDA(cudaMemcpyAsync(f + (size_t)nw * n, rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, T->stream));
-        std::vector<int> kinds(nf, 0);
-        std::vector<double> kv(nf);
-        std::vector<double*> out(nf);
-        for (int o = 0; o < nw; o++) {
-            kv[o] = std::sqrt(-2.0 * es[o]);
-            out[o] = T->ubuf.as<double>() + (size_t)o * n;
-        }
-        if (rho) {
-            kinds[nw] = 1;
-            kv[nw] = T->alpha;
-            out[nw] = vh;
-        }
-        run_convolution(*T, f, nf, kinds.data(), kv.data(), out.data());
         {
-            ProfScope ps(kProfReduce, T->stream);
-            green_reductions(*T, f, psi, T->ubuf.as<double>(), nw, es.data(), resid);
+            // one eager step on copies of psi and eps: sizes every buffer,
+            // measures the float32 bias, and checks the eigenvalues
+            DevBuf p2, e2, r2, h2;
+            p2.ensure(sizeof(double) * (size_t)nw * n);
+            e2.ensure(sizeof(double) * nw);
+            r2.ensure(sizeof(double) * nw);
+            h2.ensure(sizeof(double) * 2);
+            TAGI_CUDA(cudaMemcpyAsync(p2.p, psi, sizeof(double) * nw * n, cudaMemcpyDeviceToDevice, s));
+            TAGI_CUDA(cudaMemcpyAsync(e2.p, eps, sizeof(double) * nw, cudaMemcpyDeviceToDevice, s));
+            clear_err(*T);
+            green_step_device(*T, veff, vshift, p2.as<double>(), e2.as<double>(), nw, rho, vh, r2.as<double>(),
+                              rho ? h2.as<double>() : nullptr);
+            TAGI_REQUIRE(read_err(*T) == 0, "eps + vshift must be negative (Section 3.3)");
         }
-        for (int o = 0; o < nw; o++) eps[o] = es[o] - vshift;
-        if (rho && eh) *eh = 0.5 * weighted_dot(*T, vh, rho);
+        TAGI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
+        clear_err(*T);
+        green_step_device(*T, veff, vshift, psi, eps, nw, rho, vh, resid, rho ? eh : nullptr);
+        capturing = false;
+        TAGI_CUDA(cudaStreamEndCapture(s, &g));
+        std::unique_ptr<GreenGraph> G(new GreenGraph());
+        G->T = T;
+        TAGI_CUDA(cudaGraphInstantiate(&G->exec, g, 0));
+        size_t nn = 0;
+        TAGI_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        TAGI_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            TAGI_CUDA(cudaGraphNodeGetType(nd, &ty));
+            if (ty == cudaGraphNodeTypeKernel) G->kernels++;
+        }
+        cudaGraphDestroy(g);
+        *out = reinterpret_cast<tagi_green_graph*>(G.release());
+        return TAGI_OK;
+    } catch (const Error& e) {
+        if (capturing) {
+            cudaStreamEndCapture(s, &g);
+            cudaGetLastError();
+        }
+        if (g) cudaGraphDestroy(g);
+        return report_error(e.status, e.what());
+    } catch (...) {
+        if (g) cudaGraphDestroy(g);
+        return report_error(TAGI_ERR_CUDA, "unknown error");
+    }
+}
+
+tagi_status tagi_green_graph_launch(tagi_green_graph* graph, void* stream)
+{
+    return guarded([&] {
+        TAGI_REQUIRE(graph != nullptr, "graph is NULL");
+        GreenGraph* G = reinterpret_cast<GreenGraph*>(graph);
+        TAGI_CUDA(cudaGraphLaunch(G->exec, (cudaStream_t)stream));
+        for (int64_t i = 0; i < G->kernels; i++) note_launch();
+    });
+}
+
+tagi_status tagi_green_graph_check(tagi_green_graph* graph, void* stream)
+{
+    return guarded([&] {
+        TAGI_REQUIRE(graph != nullptr, "graph is NULL");
+        GreenGraph* G = reinterpret_cast<GreenGraph*>(graph);
+        Tree* T = G->T;
+        int h = 0;
+        TAGI_CUDA(cudaMemcpyAsync(&h, T->errflag.p, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+        TAGI_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        TAGI_REQUIRE(h == 0, "eps + vshift became non-negative during a replay (Section 3.3)");
+    });
+}
+
+tagi_status tagi_green_graph_destroy(tagi_green_graph* graph)
+{
+    return guarded([&] {
+        if (!graph) return;
+        GreenGraph* G = reinterpret_cast<GreenGraph*>(graph);
+        cudaDeviceSynchronize();
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        delete G;
     });
 }
 

@@ -49,7 +49,6 @@ __global__ void k_prepare64(const double* __restrict__ f, int nf, int64_t n, con
 
 struct EpiField {
     double* out;
-    double kval;  // k (Yukawa, the value the interaction kernel applied) or alpha (Coulomb)
     double cfac;  // factor on the analytic SS term: 1 + the kernel's measured mean bias
     int kind;
     int pad;
@@ -61,7 +60,8 @@ struct EpiFields {
 
 // One CTA per target chunk: sum the chunk's item partials in item order, add
 // the SS constant and the kernel normalisation, scatter to the caller's order.
-__global__ void k_epilogue(EpiFields E, int nf_g, int field0, int nf_tot, const int* __restrict__ tc_item0,
+__global__ void k_epilogue(EpiFields E, const double* __restrict__ kvd, int nf_g, int field0, int nf_tot,
+                           const int* __restrict__ tc_item0,
                            const int* __restrict__ tc_t0, const int* __restrict__ tc_t1, const int* __restrict__ perm,
                            const double* __restrict__ part, const float* __restrict__ c32, int64_t ldc32,
                            const double* __restrict__ c64, int64_t n, int ss)
@@ -77,11 +77,12 @@ __global__ void k_epilogue(EpiFields E, int nf_g, int field0, int nf_tot, const 
         for (int it = i0; it < i1; it++) S += part[((size_t)it * nf_tot + o) * kTargetsPerItem + threadIdx.x];
         const double c = c32 ? (double)c32[(size_t)o * ldc32 + t] : c64[(size_t)o * n + t];
         const EpiField F = E.f[g];
+        const double kv = kvd[o];  // k (Yukawa) or alpha (Coulomb), as the kernel applied them
         double u;
         if (F.kind == 0)  // G_k = e^{-kr}/(4 pi r); SS constant 4 pi c / k^2 over 4 pi
-            u = S / (4.0 * kPi) + (ss ? F.cfac * c / (F.kval * F.kval) : 0.0);
+            u = S / (4.0 * kPi) + (ss ? F.cfac * c / (kv * kv) : 0.0);
         else  // Coulomb; SS constant 2 pi alpha^2 c (Eq. correction_term)
-            u = S + (ss ? F.cfac * 2.0 * kPi * F.kval * F.kval * c : 0.0);
+            u = S + (ss ? F.cfac * 2.0 * kPi * kv * kv * c : 0.0);
         F.out[dest] = u;
     }
 }
@@ -160,18 +161,7 @@ __global__ void k_normalize(double* y, int64_t n, const double* d)
     if (i < n) y[i] /= sqrt(d[0]);
 }
 
-// eps'_o -= a_o / b_o (Eq. gradient-free); a, b interleaved in dots[2 o], dots[2 o + 1]
-__global__ void k_eps_update(double* eps, const double* dots, int nw)
-{
-    int o = threadIdx.x + blockIdx.x * blockDim.x;
-    if (o < nw) eps[o] -= dots[2 * o] / dots[2 * o + 1];
-}
 
-__global__ void k_sqrt(double* a, int n)
-{
-    int i = threadIdx.x + blockIdx.x * blockDim.x;
-    if (i < n) a[i] = sqrt(a[i]);
-}
 
 void run_dots(Tree& T, const std::vector<DotJob>& jobs, double* out_dev)
 {
@@ -209,13 +199,52 @@ void prepare_points64(Tree& T, const double* f, int nf)
     TAGI_LAUNCH_CHECK();
 }
 
-void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* kval, const double* part, double* const* out)
+// Decay rates of one call, on the device: kyd[o] = fl32(-k_o log2 e) for
+// Yukawa fields and fl32(-log2 e / alpha^2) for the Coulomb field (the
+// float32 kernel's exponent factors); kvd[o] = the k or alpha the kernel
+// therefore applies (FP32C) or the exact one (FP64).  The first n_eps fields
+// take k = sqrt(-2 (eps_o + vshift)) from device eigenvalues; a
+// non-positive eps + vshift sets *err.
+__global__ void k_make_rates(RateSrc R, const double* __restrict__ eps_dev, float* kyd, double* kvd, int* err)
+{
+    const int o = threadIdx.x + blockIdx.x * blockDim.x;
+    if (o >= R.nf) return;
+    const double L2E = 1.4426950408889634;
+    double v;
+    if (o < R.n_eps) {
+        const double es = eps_dev[o] + R.vshift;
+        if (!(es < 0.0)) atomicOr(err, 1);
+        v = sqrt(-2.0 * es);
+    } else {
+        v = R.val[o];
+    }
+    if (R.kind[o] == 0) {
+        const float ky = (float)(-v * L2E);
+        kyd[o] = ky;
+        kvd[o] = R.fp32 ? -(double)ky / L2E : v;
+    } else {
+        const float ga = (float)(-L2E / (v * v));
+        kyd[o] = ga;
+        kvd[o] = R.fp32 ? sqrt(-L2E / (double)ga) : v;
+    }
+}
+
+void make_rates(Tree& T, const RateSrc& R, const double* eps_dev)
+{
+    T.rates32.ensure(sizeof(float) * kMaxCallFields);
+    T.rates64.ensure(sizeof(double) * kMaxCallFields);
+    launch(k_make_rates, 1, kMaxCallFields, 0, T.stream, R, eps_dev, T.rates32.as<float>(), T.rates64.as<double>(),
+           T.errflag.as<int>());
+    TAGI_LAUNCH_CHECK();
+}
+
+void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* part, double* const* out)
 {
     const bool fp32 = T.prec == TAGI_FP32C;
     // FP32C: the subtracted sum c_i sum_j G~ w_j carries the mean bias beta of
     // the float32 kernel values, and cancels against the analytic SS term; the
-    // analytic term gets the same factor (1 + beta) and the Yukawa decay rate
-    // the kernel applied, so the subtraction telescopes.
+    // analytic term gets the same factor (1 + beta) and the decay rate the
+    // kernel applied (make_rates), so the subtraction telescopes.
     double by = 0.0, bg = 0.0;
     if (fp32) fp32_bias(T.stream, &by, &bg);
     for (int g0 = 0; g0 < nf; g0 += kEpiMax) {
@@ -223,16 +252,12 @@ void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* kval, cons
         EpiFields E{};
         for (int u = 0; u < g; u++) {
             const int kind = kinds[g0 + u];
-            double kv = kval[g0 + u], cf = 1.0;
-            if (fp32) {
-                kv = kind == 0 ? effective_k32(kv) : effective_alpha32(kv);
-                cf = 1.0 + (kind == 0 ? by : bg);
-            }
-            E.f[u] = EpiField{out[g0 + u], kv, cf, kind, 0};
+            const double cf = fp32 ? 1.0 + (kind == 0 ? by : bg) : 1.0;
+            E.f[u] = EpiField{out[g0 + u], cf, kind, 0};
         }
-        launch(k_epilogue, (int)T.ntchunk, kTargetsPerItem, 0, T.stream, 
-            E, g, g0, nf, T.tc_item0.as<int>(), T.tc_t0.as<int>(), T.tc_t1.as<int>(), T.perm.as<int>(), part,
-            fp32 ? T.fa.as<float>() : nullptr, T.nrec, fp32 ? nullptr : T.c64.as<double>(), T.n, T.ss);
+        launch(k_epilogue, (int)T.ntchunk, kTargetsPerItem, 0, T.stream, E, (const double*)T.rates64.as<double>(),
+               g, g0, nf, T.tc_item0.as<int>(), T.tc_t0.as<int>(), T.tc_t1.as<int>(), T.perm.as<int>(), part,
+               fp32 ? T.fa.as<float>() : nullptr, T.nrec, fp32 ? nullptr : T.c64.as<double>(), T.n, T.ss);
         TAGI_LAUNCH_CHECK();
     }
 }
@@ -243,7 +268,28 @@ void form_fields(Tree& T, const double* veff, double vshift, const double* psi, 
     TAGI_LAUNCH_CHECK();
 }
 
-void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, double* eps_s, double* resid)
+namespace {
+// eps_o -= a_o / b_o (Eq. gradient-free; the gauge shift cancels)
+__global__ void k_eps_update_dev(double* eps, const double* dots, int nw)
+{
+    int o = threadIdx.x + blockIdx.x * blockDim.x;
+    if (o < nw) eps[o] -= dots[2 * o] / dots[2 * o + 1];
+}
+__global__ void k_sqrt_copy(const double* a, double* out, int n)
+{
+    int i = threadIdx.x + blockIdx.x * blockDim.x;
+    if (i < n) out[i] = sqrt(a[i]);
+}
+__global__ void k_half(const double* a, double* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = 0.5 * a[0];
+}
+}  // namespace
+
+// Green step reductions, all on the device and without host synchronisation:
+// eps_dev (unshifted) updated in place, resid_dev[o] = ||psi_new - psi_old||_w.
+void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, double* eps_dev,
+                      double* resid_dev)
 {
     cudaStream_t s = T.stream;
     const int64_t n = T.n;
@@ -251,11 +297,9 @@ void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, 
     // psi~ = -2 u (Eq. Yukawa)
     launch(k_scale, nblocks(n * nw, 256), 256, 0, s, u, n * nw, -2.0);
     TAGI_LAUNCH_CHECK();
-    DevBuf dd;
-    dd.ensure(sizeof(double) * (3 * (size_t)nw + 8));
-    double* dots = dd.as<double>();          // 2 nw
-    double* epsd = dots + 2 * nw;            // nw
-    double* one = epsd + nw;                 // scalars
+    T.dots.ensure(sizeof(double) * (2 * (size_t)nw + 8));
+    double* dots = T.dots.as<double>();  // 2 nw
+    double* one = dots + 2 * nw;         // scalar
     // gradient-free update uses psi~ before orthogonalisation
     std::vector<DotJob> jobs;
     for (int o = 0; o < nw; o++) {
@@ -263,43 +307,35 @@ void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, 
         jobs.push_back(DotJob{u + o * n, nullptr, u + o * n, nullptr});
     }
     run_dots(T, jobs, dots);
-    TAGI_CUDA(cudaMemcpyAsync(epsd, eps_s, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
-    launch(k_eps_update, 1, 64 * ((nw + 63) / 64), 0, s, epsd, dots, nw);
+    launch(k_eps_update_dev, 1, 64 * ((nw + 63) / 64), 0, s, eps_dev, (const double*)dots, nw);
     TAGI_LAUNCH_CHECK();
     // modified Gram-Schmidt in index order under <a, b>_w
     for (int o = 0; o < nw; o++) {
         double* v = u + o * n;
         for (int p = 0; p < o; p++) {
             run_dots(T, {DotJob{v, nullptr, u + p * n, nullptr}}, one);
-            launch(k_axpy_dev, nb, 256, 0, s, u + p * n, v, n, one);
+            launch(k_axpy_dev, nb, 256, 0, s, (const double*)(u + p * n), v, n, (const double*)one);
         }
         run_dots(T, {DotJob{v, nullptr, v, nullptr}}, one);
-        launch(k_normalize, nb, 256, 0, s, v, n, one);
+        launch(k_normalize, nb, 256, 0, s, v, n, (const double*)one);
         TAGI_LAUNCH_CHECK();
     }
     // residual ||psi_new - psi_old||_w, then psi <- psi_new
     jobs.clear();
     for (int o = 0; o < nw; o++) jobs.push_back(DotJob{u + o * n, psi + o * n, u + o * n, psi + o * n});
     run_dots(T, jobs, dots);
-    launch(k_sqrt, 1, 64 * ((nw + 63) / 64), 0, s, dots, nw);
+    if (resid_dev) launch(k_sqrt_copy, 1, 64 * ((nw + 63) / 64), 0, s, (const double*)dots, resid_dev, nw);
     TAGI_CUDA(cudaMemcpyAsync(psi, u, sizeof(double) * n * nw, cudaMemcpyDeviceToDevice, s));
-    TAGI_CUDA(cudaMemcpyAsync(eps_s, epsd, sizeof(double) * nw, cudaMemcpyDeviceToHost, s));
-    std::vector<double> r(nw);
-    TAGI_CUDA(cudaMemcpyAsync(r.data(), dots, sizeof(double) * nw, cudaMemcpyDeviceToHost, s));
-    TAGI_CUDA(cudaStreamSynchronize(s));
-    if (resid)
-        for (int o = 0; o < nw; o++) resid[o] = r[o];
+    TAGI_LAUNCH_CHECK();
 }
 
-double weighted_dot(Tree& T, const double* a, const double* b)
+// eh_dev = 1/2 <vh, rho>_w on the device
+void hartree_energy(Tree& T, const double* vh, const double* rho, double* eh_dev)
 {
-    DevBuf d;
-    d.ensure(64);
-    run_dots(T, {DotJob{a, nullptr, b, nullptr}}, d.as<double>());
-    double h = 0;
-    TAGI_CUDA(cudaMemcpyAsync(&h, d.p, sizeof(double), cudaMemcpyDeviceToHost, T.stream));
-    TAGI_CUDA(cudaStreamSynchronize(T.stream));
-    return h;
+    T.dots2.ensure(sizeof(double) * 8);
+    run_dots(T, {DotJob{vh, nullptr, rho, nullptr}}, T.dots2.as<double>());
+    launch(k_half, 1, 32, 0, T.stream, (const double*)T.dots2.as<double>(), eh_dev);
+    TAGI_LAUNCH_CHECK();
 }
 
 }  // namespace tagi

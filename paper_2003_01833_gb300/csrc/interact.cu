@@ -237,13 +237,20 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
                                                            const float4* __restrict__ rec4,
                                                            const float4* __restrict__ rec4lo,
                                                            const float* __restrict__ fa, int64_t lda,
-                                                           const float* __restrict__ fb, int64_t ldb, KParams kp,
+                                                           const float* __restrict__ fb, int64_t ldb,
+                                                           const float* __restrict__ kyd,
                                                            double* __restrict__ part, int nf_tot, int field0)
 {
     constexpr int NF = NY + HH;
     constexpr int G = TileLayout<NF>::G;
     constexpr int TPT = Tpt<NF>::value;
     constexpr int THREADS = Tpt<NF>::threads;
+    // exponent factors of this launch's fields, from device memory so that a
+    // captured graph picks up the current eigenvalues on every replay
+    KParams kp{};
+#pragma unroll
+    for (int o = 0; o < NY; o++) kp.ky[o] = kyd[o];
+    if (HH) kp.ga = kyd[NY];
     __shared__ float4 srec[kTile];
     __shared__ float4 sv[G * kTile];
 
@@ -395,9 +402,10 @@ __global__ void __launch_bounds__(kThreads64) k_interact64(const Item* __restric
                                                            const double* __restrict__ rx, const double* __restrict__ ry,
                                                            const double* __restrict__ rz, const double* __restrict__ rw,
                                                            const double* __restrict__ q, const double* __restrict__ c,
-                                                           double kval, double* __restrict__ part, int nf_tot,
-                                                           int field)
+                                                           const double* __restrict__ kvd, double* __restrict__ part,
+                                                           int nf_tot, int field)
 {
+    const double kval = kvd[field];
     __shared__ double sx[kTile64], sy[kTile64], sz[kTile64], sw[kTile64], sqv[kTile64];
     const Item it = items[blockIdx.x];
     const int tid = threadIdx.x;
@@ -439,7 +447,7 @@ __global__ void __launch_bounds__(kThreads64) k_interact64(const Item* __restric
 }
 
 template <int NY, bool HH>
-void launch32_ss(Tree& T, bool ss, const KParams& kp, const float* q, const float* c, double* part, int nf_tot,
+void launch32_ss(Tree& T, bool ss, const float* kyd, const float* q, const float* c, double* part, int nf_tot,
                  int field0)
 {
     // q: rows of fa (fh for points, qh for proxies), c: rows of fb (fl for points)
@@ -448,33 +456,33 @@ void launch32_ss(Tree& T, bool ss, const KParams& kp, const float* q, const floa
     if (ss)
         launch(k_interact32<NY, HH, true>, grid, Tpt<NY + HH>::threads, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
                                                                T.cl_cen.as<double>(), T.rec4.as<float4>(),
-                                                               T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kp, part,
+                                                               T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kyd, part,
                                                                nf_tot, field0);
     else
         launch(k_interact32<NY, HH, false>, grid, Tpt<NY + HH>::threads, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
                                                                 T.cl_cen.as<double>(), T.rec4.as<float4>(),
-                                                                T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kp, part,
+                                                                T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kyd, part,
                                                                 nf_tot, field0);
     TAGI_LAUNCH_CHECK();
 }
 
 template <bool HH>
-void launch32_ny(int ny, Tree& T, bool ss, const KParams& kp, const float* q, const float* c, double* part,
+void launch32_ny(int ny, Tree& T, bool ss, const float* kyd, const float* q, const float* c, double* part,
                  int nf_tot, int field0)
 {
     switch (ny) {
         case 0:
-            if constexpr (HH) launch32_ss<0, true>(T, ss, kp, q, c, part, nf_tot, field0);
+            if constexpr (HH) launch32_ss<0, true>(T, ss, kyd, q, c, part, nf_tot, field0);
             break;
-        case 1: launch32_ss<1, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
-        case 2: launch32_ss<2, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
-        case 3: launch32_ss<3, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
-        case 4: launch32_ss<4, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
-        case 5: launch32_ss<5, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
-        case 6: launch32_ss<6, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
-        case 7: launch32_ss<7, HH>(T, ss, kp, q, c, part, nf_tot, field0); break;
+        case 1: launch32_ss<1, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
+        case 2: launch32_ss<2, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
+        case 3: launch32_ss<3, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
+        case 4: launch32_ss<4, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
+        case 5: launch32_ss<5, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
+        case 6: launch32_ss<6, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
+        case 7: launch32_ss<7, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
         case 8:
-            if constexpr (!HH) launch32_ss<8, false>(T, ss, kp, q, c, part, nf_tot, field0);
+            if constexpr (!HH) launch32_ss<8, false>(T, ss, kyd, q, c, part, nf_tot, field0);
             break;
         default: throw Error(TAGI_ERR_INVALID_ARG, "field group too large");
     }
@@ -527,36 +535,32 @@ double effective_alpha32(double a)
     return sqrt(-1.4426950408889634 / (double)ga);
 }
 
-// Fields [0, nf) of T.q32 / T.c32: Yukawa fields first (kinds[o] == 0), then
+// Fields [0, nf) of T.fa / T.fb: Yukawa fields first (kinds[o] == 0), then
 // at most one Coulomb field (kinds[o] == 1) last.  Groups of at most 8 fields
 // share a launch; the Coulomb field joins the last group when it fits.
-void interact32(Tree& T, int nf, const int* kinds, const double* kval, double* part)
+// kyd: device array of the fields' exponent factors (see make_rates).
+void interact32(Tree& T, int nf, const int* kinds, const float* kyd, double* part)
 {
     int ny = 0;
     while (ny < nf && kinds[ny] == 0) ny++;
     const bool hh = ny < nf;
     TAGI_REQUIRE(nf - ny <= 1, "at most one Coulomb field, after the Yukawa fields");
-    const float log2e = 1.4426950408889634f;
     int o = 0;
     while (o < nf) {
         int g_ny = ny - o < 8 ? ny - o : 8;
         if (g_ny < 0) g_ny = 0;
         bool g_hh = hh && (o + g_ny == ny) && g_ny < 8;
-        KParams kp{};
-        for (int u = 0; u < g_ny; u++) kp.ky[u] = (float)(-kval[o + u] * 1.4426950408889634);
-        kp.ga = hh ? (float)(-1.4426950408889634 / (kval[ny] * kval[ny])) : 0.0f;
-        (void)log2e;
         const float* q = T.fa.as<float>() + (size_t)o * T.nrec;
         const float* c = T.fb.as<float>() + (size_t)o * T.n;
         if (g_hh)
-            launch32_ny<true>(g_ny, T, T.ss != 0, kp, q, c, part, nf, o);
+            launch32_ny<true>(g_ny, T, T.ss != 0, kyd + o, q, c, part, nf, o);
         else
-            launch32_ny<false>(g_ny, T, T.ss != 0, kp, q, c, part, nf, o);
+            launch32_ny<false>(g_ny, T, T.ss != 0, kyd + o, q, c, part, nf, o);
         o += g_ny + (g_hh ? 1 : 0);
     }
 }
 
-void interact64(Tree& T, int field, int nf_tot, int kind, double kval, const double* q, const double* c,
+void interact64(Tree& T, int field, int nf_tot, int kind, const double* kvd, const double* q, const double* c,
                 double* part)
 {
     const int grid = (int)T.nitems;
@@ -566,14 +570,14 @@ void interact64(Tree& T, int field, int nf_tot, int kind, double kval, const dou
     const double *rx = T.rx.as<double>(), *ry = T.ry.as<double>(), *rz = T.rz.as<double>(), *rw = T.rw.as<double>();
     if (kind == 0) {
         if (T.ss)
-            launch(k_interact64<0, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kval, part, nf_tot, field);
+            launch(k_interact64<0, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, nf_tot, field);
         else
-            launch(k_interact64<0, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kval, part, nf_tot, field);
+            launch(k_interact64<0, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, nf_tot, field);
     } else {
         if (T.ss)
-            launch(k_interact64<1, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kval, part, nf_tot, field);
+            launch(k_interact64<1, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, nf_tot, field);
         else
-            launch(k_interact64<1, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kval, part, nf_tot, field);
+            launch(k_interact64<1, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, nf_tot, field);
     }
     TAGI_LAUNCH_CHECK();
 }

@@ -102,6 +102,17 @@ constexpr int kMaxDegree = 9;
 constexpr int kTargetsPerItem = 256;  // targets of one work item (one CTA)
 constexpr int kAntChunk = 2048;       // points per anterpolation work item
 
+// Decay rates of one call (make_rates): the first n_eps fields take
+// k = sqrt(-2 (eps + vshift)) from device eigenvalues, the others val[o]
+// (k for Yukawa, alpha for Coulomb).  kind[o]: 0 Yukawa, 1 Coulomb.
+constexpr int kMaxCallFields = 128;
+struct RateSrc {
+    int nf, n_eps, fp32, pad;
+    double vshift;
+    double val[kMaxCallFields];
+    int kind[kMaxCallFields];
+};
+
 // Interaction entry: a contiguous range of source records [src0, src1) seen
 // from a batch.  frame: cluster whose center the records' local coordinates
 // are relative to (FP32 path).  flags bit0: the range holds the batch's own
@@ -180,6 +191,11 @@ struct Tree {
     DevBuf part;        // double partial sums
     DevBuf antpart;     // double anterpolation partials
     DevBuf scratch;     // general scratch (reductions)
+    DevBuf rates32;     // float [kMaxCallFields] exponent factors of the current call
+    DevBuf rates64;     // double [kMaxCallFields] k or alpha as applied by the kernels
+    DevBuf errflag;     // int: set by device-side argument checks (make_rates)
+    DevBuf dots, dots2; // double: Green-step inner products
+    DevBuf epsd, residd, ehd;  // double: device copies for the host-value entry point
     DevBuf fbuf;        // double [nf][n] formed fields (Green step)
     DevBuf ubuf;        // double [nf][n] convolution results (Green step)
 
@@ -194,8 +210,8 @@ void anterpolate_fields64(Tree& T, int nf);
 void anterpolate_all_clusters64(Tree& T, const double* q, int nq, double* qh);
 // interact.cu
 // kinds[o]: 0 = Yukawa with kval[o], 1 = Coulomb/Hartree
-void interact32(Tree& T, int nf, const int* kinds, const double* kval, double* part);
-void interact64(Tree& T, int field, int nf_tot, int kind, double kval, const double* q, const double* c,
+void interact32(Tree& T, int nf, const int* kinds, const float* kyd, double* part);
+void interact64(Tree& T, int field, int nf_tot, int kind, const double* kvd, const double* q, const double* c,
                 double* part);
 // mean relative bias of the float32 Yukawa and Gaussian kernel values (measured)
 void fp32_bias(cudaStream_t s, double* beta_y, double* beta_g);
@@ -204,15 +220,18 @@ double effective_alpha32(double a);
 // green.cu
 void prepare_points32(Tree& T, const double* f, int nf);   // fa, fb, qant from caller-order fields
 void prepare_points64(Tree& T, const double* f, int nf);   // q64 from caller-order fields
-// u[o][caller i] for o in [0, nf): kinds[o] 0 = Yukawa (k = kval[o]), 1 = Coulomb (alpha = kval[o]).
-// out[o] points to the caller-order output row of field o.
-void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* kval, const double* part,
-                     double* const* out);
-// Green step reductions on caller-order rows (all float64):
-//   f (nw x n), psi (nw x n, in: old, out: new), u (nw x n, in: Yukawa results,
-//   clobbered), eps_s (host, shifted eigenvalues, updated), resid (host or null).
-void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, double* eps_s, double* resid);
-double weighted_dot(Tree& T, const double* a, const double* b);
+// rates of a call into T.rates32 / T.rates64 (see RateSrc)
+void make_rates(Tree& T, const RateSrc& R, const double* eps_dev);
+// u[o][caller i] for o in [0, nf): kinds[o] 0 = Yukawa, 1 = Coulomb, with the
+// rates of the last make_rates.  out[o] points to the caller-order output row.
+void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* part, double* const* out);
+void form_fields(Tree& T, const double* veff, double vshift, const double* psi, int nw, double* f);
+// Green step reductions on caller-order rows, all on the device:
+//   f (nw x n), psi (nw x n, in: old, out: new), u (nw x n, in: Yukawa
+//   results, clobbered), eps_dev (nw, unshifted, updated), resid_dev (nw or null).
+void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, double* eps_dev,
+                      double* resid_dev);
+void hartree_energy(Tree& T, const double* vh, const double* rho, double* eh_dev);
 
 // sets the message tagi_last_error returns on this thread; returns status
 tagi_status report_error(tagi_status status, const char* msg);

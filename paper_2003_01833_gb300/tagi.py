@@ -76,6 +76,15 @@ def lib():
         L.tagi_kernel_launches.restype = ctypes.c_int64
         L.tagi_profile_enable.argtypes = [ctypes.c_int]
         L.tagi_fp32_bias.argtypes = [_D, _D, _vp]
+        L.tagi_green_graph_create.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                              _vp, ctypes.POINTER(_vp)]
+        L.tagi_green_graph_launch.argtypes = [_vp, _vp]
+        L.tagi_green_graph_check.argtypes = [_vp, _vp]
+        L.tagi_green_graph_destroy.argtypes = [_vp]
+        L.tagi_trim_cache.argtypes = []
+        for name in ("tagi_green_graph_create", "tagi_green_graph_launch", "tagi_green_graph_check",
+                     "tagi_green_graph_destroy", "tagi_trim_cache"):
+            getattr(L, name).restype = ctypes.c_int
         L.tagi_yukawa_direct_noalloc.argtypes = [_vp, _vp, _vp, _D, ctypes.c_int, ctypes.c_int64, _vp, _vp]
         L.tagi_yukawa_direct_noalloc.restype = ctypes.c_int
         L.tagi_profile_read.argtypes = [ctypes.c_int, _D, _I64]
@@ -273,6 +282,39 @@ def tagi_yukawa_direct_noalloc(xyz, w, f, k, u, stream=None):
         raise ValueError("one k per field")
     _check(lib().tagi_yukawa_direct_noalloc(_dptr(xyz, "xyz", 3 * n), _dptr(w, "w", n), _dptr(f, "f", nf * n), kp,
                                             nf, n, _dptr(u, "u", nf * n), _stream(stream)))
+
+
+def tagi_green_graph_create(tree, veff, vshift, psi, eps, resid, rho=None, vh=None, eh=None, stream=None):
+    """Capture one Green iteration as a CUDA graph.  psi (nw, n), eps (nw,),
+    resid (nw,), veff/rho/vh (n,), eh (1,): float64 CUDA tensors, all kept
+    by the graph (replays update psi and eps in place)."""
+    nw = psi.shape[0] if psi.dim() == 2 else 1
+    n = _tree_n(tree)
+    if psi.numel() != nw * n or eps.numel() != nw or resid.numel() != nw or veff.numel() != n:
+        raise ValueError("psi (nw, n), eps (nw,), resid (nw,), veff (n,)")
+    if rho is not None and (rho.numel() != n or vh is None or vh.numel() != n or eh is None or eh.numel() < 1):
+        raise ValueError("rho and vh (n,) and eh (1,) go together")
+    h = ctypes.c_void_p()
+    _check(lib().tagi_green_graph_create(tree, _dptr(veff, "veff"), float(vshift), _dptr(psi, "psi"), _dptr(eps, "eps"),
+                                         nw, _dptr(rho, "rho"), _dptr(vh, "vh"), _dptr(resid, "resid"),
+                                         _dptr(eh, "eh"), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def tagi_green_graph_launch(graph, stream=None):
+    _check(lib().tagi_green_graph_launch(graph, _stream(stream)))
+
+
+def tagi_green_graph_check(graph, stream=None):
+    _check(lib().tagi_green_graph_check(graph, _stream(stream)))
+
+
+def tagi_green_graph_destroy(graph):
+    _check(lib().tagi_green_graph_destroy(graph))
+
+
+def tagi_trim_cache():
+    _check(lib().tagi_trim_cache())
 
 
 def tagi_last_error():

@@ -265,6 +265,49 @@ def test_fp32_kernel_bias_is_measured(T):
     assert T.tagi_fp32_bias() == (by, bg)
 
 
+def test_green_graph_replays_match_eager_steps(T):
+    """Three replays of the captured Green iteration give exactly what three
+    eager tagi_green_step calls give (same kernels in the same order)."""
+    wl = W.hydrogen_1s(seed=3, ncell=10)
+    m = wl.mesh
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side), build(T, m.xyz, m.w, theta=0.7, degree=6, leaf_size=1000,
+                                        prec=T.TAGI_FP32C) as tr:
+        veff, rho = dev(wl.veff), dev(wl.rho)
+        psi_e = dev(wl.psi)
+        vh_e = torch.empty(wl.n, dtype=torch.float64, device="cuda")
+        eps_e = np.array(wl.eps, dtype=np.float64)
+        for _ in range(3):
+            eps_e, res_e, eh_e = T.tagi_green_step(tr.handle, veff, wl.vshift, psi_e, eps_e, rho=rho, vh=vh_e)
+        psi_g = dev(wl.psi)
+        eps_g = dev(wl.eps)
+        res_g = torch.empty(1, dtype=torch.float64, device="cuda")
+        vh_g = torch.empty(wl.n, dtype=torch.float64, device="cuda")
+        eh_g = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = T.tagi_green_graph_create(tr.handle, veff, wl.vshift, psi_g, eps_g, res_g, rho=rho, vh=vh_g, eh=eh_g)
+        try:
+            np.testing.assert_array_equal(psi_g.cpu().numpy(), wl.psi)  # creation leaves the inputs alone
+            for _ in range(3):
+                T.tagi_green_graph_launch(g)
+            T.tagi_green_graph_check(g)
+        finally:
+            T.tagi_green_graph_destroy(g)
+        np.testing.assert_array_equal(psi_g.cpu().numpy(), psi_e.cpu().numpy())
+        np.testing.assert_array_equal(eps_g.cpu().numpy(), eps_e)
+        np.testing.assert_array_equal(res_g.cpu().numpy(), res_e)
+        assert eh_g.item() == eh_e
+
+
+def test_green_graph_needs_a_created_stream(T):
+    wl = W.hydrogen_1s(seed=3)
+    with build(T, wl.mesh.xyz, wl.mesh.w, theta=0.7, degree=4, leaf_size=2000, prec=T.TAGI_FP32C) as tr:
+        p = dev(wl.psi)
+        e = dev(wl.eps)
+        r = torch.empty(1, dtype=torch.float64, device="cuda")
+        with pytest.raises(T.TagiError):
+            T.tagi_green_graph_create(tr.handle, dev(wl.veff), 0.0, p, e, r, stream=0)
+
+
 # ------------------------------------------------------------------ edge cases
 def test_single_point(T):
     """One point: no pair survives r != 0, only the SS constants remain."""
