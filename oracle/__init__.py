@@ -244,3 +244,116 @@ def green_step(tree, theta, degree, w, veff, vshift, psi, eps, rho=None, alpha=1
         out["vh"] = vh
         out["eh"] = 0.5 * np.sum(vh * rho * w)
     return out
+
+
+# --------------------------------------------------------------------------
+# Green Iteration loop with Anderson mixing of eigenpairs (Algorithm 2,
+# Section 4.3 "Wavefunction Mixing")
+# --------------------------------------------------------------------------
+
+
+def anderson_mix(X, F, beta, wx):
+    """Anderson mixing (Anderson 1965) of a fixed-point iteration x -> g(x).
+
+    X, F: arrays (m+1, L) of the last m+1 inputs x_j and residuals
+    F_j = g(x_j) - x_j, oldest first; wx: weights of the inner product
+    (a, b) = sum a b wx.  With D_j = F_n - F_{n-j} (j = 1..m), theta solves
+    the normal equations of min ||F_n - sum_j theta_j D_j||, and
+        x_bar = x_n - sum_j theta_j (x_n - x_{n-j}),
+        F_bar = F_n - sum_j theta_j D_j,
+        x_next = x_bar + beta F_bar.
+    One entry (m = 0) gives simple mixing x_n + beta F_n.  A numerically
+    singular Gram matrix (condition number above 1e13) also falls back to
+    simple mixing.
+    """
+    X = np.atleast_2d(np.asarray(X, np.float64))
+    F = np.atleast_2d(np.asarray(F, np.float64))
+    xn, fn = X[-1], F[-1]
+    m = X.shape[0] - 1
+    if m == 0:
+        return xn + beta * fn
+    D = fn[None, :] - F[-2::-1]    # D_j = F_n - F_{n-j}, j = 1..m
+    DX = xn[None, :] - X[-2::-1]   # x_n - x_{n-j}
+    A = (D * wx[None, :]) @ D.T
+    b = (D * wx[None, :]) @ fn
+    if not np.all(np.isfinite(A)) or np.linalg.cond(A) > 1e13:
+        return xn + beta * fn
+    th = np.linalg.solve(A, b)
+    x_bar = xn - th @ DX
+    f_bar = fn - th @ D
+    return x_bar + beta * f_bar
+
+
+def green_iterate(tree, theta, degree, w, veff, vshift, psi, eps, tol_gi, max_iter, beta=0.5, history=5,
+                  mix_tol=np.inf):
+    """Green Iteration for all orbitals at once (Algorithm 2, batched as in
+    green_step), with Anderson mixing of each eigenpair x = (eps, psi) under
+    (x1, x2) = eps1 eps2 + sum psi1 psi2 w (Section 4.3).
+
+    Each step, for every orbital not yet converged:
+      line 3: psi~ = G(eps) psi (treecode Yukawa with SS, psi~ = -2 u);
+      line 4: eps' = eps - <(V+V_shift) psi, psi - psi~>_w / <psi~, psi~>_w;
+      lines 5-6: orthogonalise psi~ in index order against every lower-index
+        orbital (the new iterate of an active one, the stored pair of a
+        converged one) and normalise: g(x) = (eps', psi');
+      line 7: r = ||psi' - psi||_w.  If r < tol_gi the orbital is converged and
+        keeps its step input (eps^(n), psi^(n)), as Algorithm 2 stores it.
+    Otherwise the next input is g(x), or, once the orbital's residual has
+    fallen below mix_tol (mixing stays on from then), the Anderson update of
+    its last history+1 pairs (x_j, F_j = g(x_j) - x_j) with parameter beta.
+
+    Returns psi, eps, resid (last residual per orbital), iters (the step count
+    at which each orbital converged, -1 if it did not), steps, field_steps
+    (sum over steps of the orbitals convolved).
+    """
+    psi = np.array(np.atleast_2d(psi), np.float64)
+    eps = np.array(eps, np.float64)
+    nw, n = psi.shape
+    vs = veff + vshift
+    wx = np.concatenate([[1.0], w])
+    conv = np.zeros(nw, bool)
+    mixing = np.zeros(nw, bool)
+    iters = np.full(nw, -1)
+    resid = np.full(nw, np.nan)
+    hx = [[] for _ in range(nw)]
+    hf = [[] for _ in range(nw)]
+    steps = field_steps = 0
+    for step in range(max_iter):
+        act = np.flatnonzero(~conv)
+        if act.size == 0:
+            break
+        steps += 1
+        field_steps += act.size
+        e_new, pt = {}, {}
+        for o in act:
+            if not eps[o] + vshift < 0.0:
+                raise ValueError("eps + V_shift must stay negative (Section 3.3)")
+            k = np.sqrt(-2.0 * (eps[o] + vshift))
+            pt[o] = -2.0 * treecode_yukawa(tree, theta, degree, vs * psi[o], k, w, ss=True)
+            e_new[o] = eps[o] - np.sum(vs * psi[o] * (psi[o] - pt[o]) * w) / np.sum(pt[o] * pt[o] * w)
+        q = {}
+        for o in act:
+            v = pt[o].copy()
+            for p in range(o):
+                b = q[p] if p in q else psi[p]
+                v -= np.sum(v * b * w) * b
+            q[o] = v / np.sqrt(np.sum(v * v * w))
+        for o in act:
+            f_psi = q[o] - psi[o]
+            resid[o] = np.sqrt(np.sum(f_psi * f_psi * w))
+            if resid[o] < tol_gi:
+                conv[o] = True
+                iters[o] = step + 1
+                continue
+            if resid[o] < mix_tol:
+                mixing[o] = True
+            if mixing[o]:
+                hx[o].append(np.concatenate([[eps[o]], psi[o]]))
+                hf[o].append(np.concatenate([[e_new[o] - eps[o]], f_psi]))
+                hx[o] = hx[o][-(history + 1):]
+                hf[o] = hf[o][-(history + 1):]
+                x = anderson_mix(np.array(hx[o]), np.array(hf[o]), beta, wx)
+                eps[o], psi[o] = x[0], x[1:]
+            else:
+                eps[o], psi[o] = e_new[o], q[o]
+    return {"psi": psi, "eps": eps, "resid": resid, "iters": iters, "steps": steps, "field_steps": field_steps}

@@ -210,6 +210,60 @@ def v_hartree0(mol: Molecule, pts: np.ndarray) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# LDA exchange-correlation (Section 2, the LDA of Ceperley-Alder as
+# parametrised by Perdew and Zunger; Libxc is not available, so the published
+# spin-unpolarised formulas are written out here).  Input preparation only:
+# V_eff enters the convolutions as data.
+# --------------------------------------------------------------------------
+
+# correlation fit parameters: r_s >= 1 (gamma, beta1, beta2), r_s < 1 (A, B, C, D)
+PZ81_LOW_DENSITY = (-0.1423, 1.0529, 0.3334)
+PZ81_HIGH_DENSITY = (0.0311, -0.048, 0.0020, -0.0116)
+
+
+def lda_xc(rho: np.ndarray):
+    """Exchange-correlation energy per electron eps_xc and potential
+    v_xc = d(rho eps_xc)/d rho of the spin-unpolarised LDA.
+
+    Exchange (Dirac/Slater): eps_x = -(3/4)(3 rho/pi)^(1/3), v_x = (4/3) eps_x.
+    Correlation in r_s = (3/(4 pi rho))^(1/3):
+      r_s >= 1: eps_c = gamma/(1 + b1 sqrt(r_s) + b2 r_s),
+                v_c = eps_c (1 + 7/6 b1 sqrt(r_s) + 4/3 b2 r_s)/(1 + b1 sqrt(r_s) + b2 r_s);
+      r_s < 1:  eps_c = A ln r_s + B + C r_s ln r_s + D r_s,
+                v_c = A ln r_s + (B - A/3) + 2/3 C r_s ln r_s + (2 D - C)/3 r_s.
+    Points with rho <= 1e-30 get zero.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    ex = np.zeros_like(rho)
+    ec = np.zeros_like(rho)
+    vx = np.zeros_like(rho)
+    vc = np.zeros_like(rho)
+    m = rho > 1e-30
+    r = rho[m]
+    ex[m] = -0.75 * np.cbrt(3.0 * r / math.pi)
+    vx[m] = 4.0 / 3.0 * ex[m]
+    rs = np.cbrt(3.0 / (4.0 * math.pi * r))
+    g, b1, b2 = PZ81_LOW_DENSITY
+    A, B, C, D = PZ81_HIGH_DENSITY
+    lo = rs >= 1.0
+    sq = np.sqrt(rs[lo])
+    den = 1.0 + b1 * sq + b2 * rs[lo]
+    e_lo = g / den
+    v_lo = e_lo * (1.0 + 7.0 / 6.0 * b1 * sq + 4.0 / 3.0 * b2 * rs[lo]) / den
+    rh = rs[~lo]
+    ln = np.log(rh)
+    e_hi = A * ln + B + C * rh * ln + D * rh
+    v_hi = A * ln + (B - A / 3.0) + 2.0 / 3.0 * C * rh * ln + (2.0 * D - C) / 3.0 * rh
+    ecm = np.empty_like(r)
+    vcm = np.empty_like(r)
+    ecm[lo], ecm[~lo] = e_lo, e_hi
+    vcm[lo], vcm[~lo] = v_lo, v_hi
+    ec[m] = ecm
+    vc[m] = vcm
+    return ex + ec, vx + vc
+
+
+# --------------------------------------------------------------------------
 # Adaptive refinement (Section 3.2, Eq. refinement_criterion)
 # --------------------------------------------------------------------------
 
@@ -385,6 +439,26 @@ def hydrogen_1s(seed: int = 0, ncell: int = 8, p: int = 3, half_width: float = 1
                     leaf_size=2000, meta={"nucleus": R.tolist(), "seed": seed})
 
 
+def hydrogen_adaptive(seed: int = 0, tol_m: float = 1e-3, p: int = 4, half_width: float = 20.0,
+                      uniform_levels: int = 2) -> Workload:
+    """Hydrogen on an adaptive mesh (Section 3.2) that resolves the nucleus:
+    the nucleus sits at the origin, a cell vertex on every level, so no
+    quadrature node of the refinement coincides with it.  The seed picks a
+    1% smooth perturbation of psi (none for seed 0).  V = -1/r,
+    psi = e^{-r}/sqrt(pi), eps = -0.5, V_shift = 0."""
+    rng = np.random.default_rng(seed)
+    R = np.zeros(3)
+    mol = Molecule(["H"], R[None, :])
+    mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
+    r = _dist(mesh.xyz.T, R)
+    psi = np.exp(-r) / math.sqrt(math.pi)
+    if seed:
+        psi = psi * _smooth_perturbation(rng, mesh.xyz.T)
+    return Workload(name=f"H-adaptive-{mesh.n}", mesh=mesh, veff=-1.0 / r, psi=psi[None, :],
+                    eps=np.array([-0.5]), rho=psi * psi, vshift=0.0, theta=0.7, degree=6, leaf_size=2000,
+                    meta={"nucleus": R.tolist(), "seed": seed, "tol_m": tol_m})
+
+
 def _smooth_perturbation(rng, pts, amp=0.01):
     a = rng.normal(size=3)
     a *= 0.5 / np.linalg.norm(a)
@@ -396,7 +470,8 @@ def lithium(seed: int = 1, tol_m: float = 3e-7, p: int = 4, half_width: float = 
             uniform_levels: int = 3) -> Workload:
     """Li atom at the origin: adaptive mesh on [-20,20]^3, p = 4, two occupied
     orbitals (hydrogenic 1s and 2s with Z = 3, the 2s with a seeded 1% smooth
-    perturbation), V_eff = V_ext + V_H[rho0], Hartree source rho0.  The
+    perturbation), V_eff = V_ext + V_H[rho0] + V_xc^LDA[rho0], Hartree source
+    rho0.  The
     default tolerance 3e-7 gives about 309k points (1e-5 gives 162k with this
     test function)."""
     mol = Molecule(["Li"], np.zeros((1, 3)))
@@ -407,7 +482,7 @@ def lithium(seed: int = 1, tol_m: float = 3e-7, p: int = 4, half_width: float = 
     psi1 = radial_orbital("1s", 3.0, r)
     psi2 = radial_orbital("2s", 3.0, r) * _smooth_perturbation(rng, pts)
     rho = density0(mol, pts)
-    veff = v_ext(mol, pts) + v_hartree0(mol, pts)
+    veff = v_ext(mol, pts) + v_hartree0(mol, pts) + lda_xc(rho)[1]
     eps = np.array([-1.9, -0.11]) + rng.uniform(-0.02, 0.02, size=2)
     return Workload(name="Li", mesh=mesh, veff=veff, psi=np.stack([psi1, psi2]), eps=eps,
                     rho=rho, vshift=-0.5, theta=0.7, degree=8, leaf_size=2000,
@@ -452,7 +527,7 @@ def _molecule_workload(name, mol, mesh, seed, n_orb):
     coef = rng.normal(size=(n_orb, basis.shape[0]))
     psi = coef @ basis
     rho = density0(mol, pts)
-    veff = v_ext(mol, pts) + v_hartree0(mol, pts)
+    veff = v_ext(mol, pts) + v_hartree0(mol, pts) + lda_xc(rho)[1]
     eps = np.sort(rng.uniform(-20.0, -0.3, size=n_orb))
     return Workload(name=name, mesh=mesh, veff=veff, psi=psi, eps=eps, rho=rho, vshift=-0.5,
                     theta=0.7, degree=8, leaf_size=2000, meta={"seed": seed, "n_orb": n_orb})

@@ -1,0 +1,139 @@
+"""Pins of the oracle's Green Iteration loop and Anderson mixing (Algorithm 2,
+Section 4.3).
+
+- Anderson mixing with one history entry is simple mixing x + beta F.
+- On a linear fixed-point problem x = M x + b in d dimensions, Anderson
+  mixing with unlimited history and beta = 1 is equivalent to GMRES (Walker
+  and Ni, SIAM J. Numer. Anal. 49, 2011), so it reaches the solution of
+  (I - M) x = b after at most d + 1 steps. A sign or index slip in the normal
+  equations or in the update breaks that finite termination.
+- The eigenvalue is part of the mixed vector: with the orbital fixed and eps
+  following an affine map, the secant step lands on the fixed point in two
+  steps only if the eps component enters the inner product.
+- One loop step with mixing off is the batched Green step.
+- Hydrogen on an adaptive mesh: with and without mixing the loop converges
+  to one fixed point, within the mesh's discretisation error of eps = -0.5 Ha;
+  mixing takes fewer steps.
+- Converged orbitals keep their step input and stay fixed; the others stay
+  orthogonal to them.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_01833_gb300 import workloads as W
+
+
+def _run_linear(M, b, beta, history, steps):
+    d = len(b)
+    wx = np.ones(d)
+    x = np.zeros(d)
+    X, F = [], []
+    out = []
+    for _ in range(steps):
+        f = M @ x + b - x
+        X.append(x.copy())
+        F.append(f)
+        X, F = X[-(history + 1):], F[-(history + 1):]
+        x = oracle.anderson_mix(np.array(X), np.array(F), beta, wx)
+        out.append(x.copy())
+    return out
+
+
+def test_anderson_one_entry_is_simple_mixing():
+    rng = np.random.default_rng(0)
+    x, f, wx = rng.normal(size=7), rng.normal(size=7), rng.uniform(0.5, 2, size=7)
+    np.testing.assert_array_equal(oracle.anderson_mix(x[None], f[None], 0.3, wx), x + 0.3 * f)
+
+
+@pytest.mark.parametrize("d", [3, 6])
+def test_anderson_linear_problem_terminates_like_gmres(d):
+    rng = np.random.default_rng(d)
+    Q, _ = np.linalg.qr(rng.normal(size=(d, d)))
+    M = Q @ np.diag(rng.uniform(-0.9, 0.9, size=d)) @ Q.T + 0.05 * rng.normal(size=(d, d))
+    b = rng.normal(size=d)
+    xstar = np.linalg.solve(np.eye(d) - M, b)
+    xs = _run_linear(M, b, beta=1.0, history=100, steps=d + 1)
+    assert np.linalg.norm(xs[d] - xstar) < 1e-9 * np.linalg.norm(xstar)
+    # simple mixing (history 0) is still far away after d + 1 steps
+    ys = _run_linear(M, b, beta=1.0, history=0, steps=d + 1)
+    assert np.linalg.norm(ys[d] - xstar) > 1e-4 * np.linalg.norm(xstar)
+
+
+def test_anderson_mixes_the_eigenvalue_component():
+    """x = (eps, psi) with psi already a fixed point and eps -> 0.5 eps + 1:
+    two steps land on eps = 2 (a secant step on the 1-D affine map)."""
+    n = 5
+    w = np.full(n, 0.2)
+    wx = np.concatenate([[1.0], w])
+    psi = np.ones(n)
+    eps = 0.0
+    X, F = [], []
+    for _ in range(2):
+        X.append(np.concatenate([[eps], psi]))
+        F.append(np.concatenate([[0.5 * eps + 1.0 - eps], np.zeros(n)]))
+        x = oracle.anderson_mix(np.array(X), np.array(F), 0.5, wx)
+        eps, psi = x[0], x[1:]
+    assert abs(eps - 2.0) < 1e-14
+    np.testing.assert_array_equal(psi, np.ones(n))
+
+
+def _h_mesh():
+    wl = W.hydrogen_adaptive()  # 36,000 points, nucleus at the origin
+    r = np.sqrt(np.sum(wl.mesh.xyz**2, axis=0))
+    return wl, oracle.Tree(wl.mesh.xyz, 2000), wl.mesh.w, r
+
+
+def _normalised(v, w):
+    return v / np.sqrt(np.sum(v * v * w))
+
+
+def test_one_step_is_the_green_step():
+    wl, T, w, r = _h_mesh()
+    p0 = _normalised(np.exp(-r), w)
+    psi0 = np.stack([p0, _normalised((2.0 - r) * np.exp(-0.5 * r), w)])
+    eps0 = np.array([-0.5, -0.125])
+    a = oracle.green_step(T, 0.7, 6, w, wl.veff, -0.5, psi0, eps0)
+    b = oracle.green_iterate(T, 0.7, 6, w, wl.veff, -0.5, psi0, eps0, tol_gi=0.0, max_iter=1, mix_tol=0.0)
+    np.testing.assert_array_equal(a["psi"], b["psi"])
+    # the Green step subtracts the shift after the update: one rounding apart
+    np.testing.assert_allclose(a["eps"], b["eps"], rtol=1e-14)
+    np.testing.assert_array_equal(a["resid"], b["resid"])
+    assert b["steps"] == 1 and b["field_steps"] == 2 and np.all(b["iters"] == -1)
+
+
+def test_hydrogen_loop_converges_with_and_without_mixing():
+    """From psi = e^{-0.7 r}, eps = -0.4 both loops reach one fixed point,
+    eps = -0.5 Ha up to the mesh's discretisation error (2.5e-3 on this mesh;
+    4.7e-4 at tol_m = 1e-4), and mixing (beta = 0.5) takes fewer steps."""
+    wl, T, w, r = _h_mesh()
+    psi0 = _normalised(np.exp(-0.7 * r), w)[None]
+    eps0 = np.array([-0.4])
+    plain = oracle.green_iterate(T, 0.7, 6, w, wl.veff, 0.0, psi0, eps0, tol_gi=1e-5, max_iter=40, mix_tol=0.0)
+    mixed = oracle.green_iterate(T, 0.7, 6, w, wl.veff, 0.0, psi0, eps0, tol_gi=1e-5, max_iter=40, beta=0.5)
+    assert plain["iters"][0] > 0 and mixed["iters"][0] > 0
+    assert mixed["iters"][0] < plain["iters"][0]
+    assert abs(plain["eps"][0] - mixed["eps"][0]) < 1e-5
+    assert np.sqrt(np.sum((plain["psi"][0] - mixed["psi"][0]) ** 2 * w)) < 1e-4
+    assert abs(plain["eps"][0] + 0.5) < 5e-3
+
+
+def test_converged_orbitals_stay_fixed_and_others_orthogonal():
+    """1s and 2s of hydrogen (eps -0.5 and -0.125 Ha): the 1s converges
+    first, keeps the input of its converging step, and the 2s stays
+    orthogonal to it."""
+    wl, T, w, r = _h_mesh()
+    p0 = _normalised(np.exp(-r), w)
+    p1 = (2.0 - r) * np.exp(-0.5 * r)
+    p1 = _normalised(p1 - np.sum(p1 * p0 * w) * p0, w)
+    psi0 = np.stack([p0, p1])
+    eps0 = np.array([-0.5, -0.125])
+    a = oracle.green_iterate(T, 0.7, 6, w, wl.veff, -0.5, psi0, eps0, tol_gi=3e-4, max_iter=8, mix_tol=0.0)
+    it0 = a["iters"][0]
+    assert 0 < it0 < a["steps"] and a["iters"][1] == -1
+    assert a["field_steps"] == it0 + a["steps"]
+    b = oracle.green_iterate(T, 0.7, 6, w, wl.veff, -0.5, psi0, eps0, tol_gi=0.0, max_iter=it0 - 1, mix_tol=0.0)
+    np.testing.assert_array_equal(a["psi"][0], b["psi"][0])
+    np.testing.assert_array_equal(a["eps"][0], b["eps"][0])
+    assert abs(np.sum(a["psi"][0] * a["psi"][1] * w)) < 1e-12
+    assert abs(a["eps"][0] + 0.5) < 5e-3 and abs(a["eps"][1] + 0.125) < 5e-3

@@ -85,3 +85,40 @@ def test_radial_hartree_table_gauss_law():
     """Far from the atom the Hartree potential is N_e / r."""
     r = np.array([60.0])
     assert abs(W.atomic_hartree("Li", r)[0] - 3.0 / 60.0) < 1e-6
+
+
+def test_lda_exchange_in_rs_form():
+    """eps_x = -(3/(4 pi)) (9 pi/4)^(1/3) / r_s = -0.4581652932831429 / r_s Ha,
+    the textbook r_s form, against the rho^(1/3) form the module evaluates."""
+    for rs in (0.3, 1.0, 2.5, 7.0):
+        rho = 3.0 / (4.0 * math.pi * rs**3)
+        ex_rs = -0.4581652932831429 / rs
+        # correlation is small; isolate exchange by its 4/3 ratio to v_x
+        e, v = W.lda_xc(np.array([rho]))
+        g, b1, b2 = W.PZ81_LOW_DENSITY
+        A, B, C, D = W.PZ81_HIGH_DENSITY
+        if rs >= 1:
+            ec = g / (1 + b1 * math.sqrt(rs) + b2 * rs)
+        else:
+            ec = A * math.log(rs) + B + C * rs * math.log(rs) + D * rs
+        assert abs((e[0] - ec) - ex_rs) < 1e-13 * abs(ex_rs)
+
+
+def test_lda_potential_is_the_density_derivative():
+    """v_xc = d(rho eps_xc)/d rho, by central differences on both branches
+    of the correlation fit (r_s from 0.1 to 20)."""
+    rs = np.array([0.1, 0.4, 0.9, 1.2, 3.0, 8.0, 20.0])
+    rho = 3.0 / (4.0 * np.pi * rs**3)
+    e, v = W.lda_xc(rho)
+    h = 1e-6 * rho
+    ep, _ = W.lda_xc(rho + h)
+    em, _ = W.lda_xc(rho - h)
+    dnum = ((rho + h) * ep - (rho - h) * em) / (2 * h)
+    np.testing.assert_allclose(v, dnum, rtol=1e-7)
+    # the two correlation branches meet at r_s = 1 to the fit's 4e-5 Ha
+    lo, _ = W.lda_xc(np.array([3.0 / (4.0 * np.pi) * (1 - 1e-12)]))
+    hi, _ = W.lda_xc(np.array([3.0 / (4.0 * np.pi) * (1 + 1e-12)]))
+    assert abs(lo[0] - hi[0]) < 5e-5
+    # zero density gives zero
+    e0, v0 = W.lda_xc(np.zeros(2))
+    assert np.all(e0 == 0) and np.all(v0 == 0)
