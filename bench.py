@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--impl", default="tagi", choices=["tagi", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain-form comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-loop", action="store_true", help="skip the Green Iteration loop leg")
     ap.add_argument("--workload", default="li", choices=["li", "li-small"],
                     help="li: the benchmark workload (309k points); li-small: tol_m 1e-3 mesh (99k) for profiling")
     ap.add_argument("--profile-case", action="store_true",
@@ -293,6 +294,34 @@ def graph_replay(T, args, wl, xyz, w, params, veff, rho, vh, psi0, flush, inter,
             "note": "tree built once; each replay is one whole Green iteration (a3-a8) from a CUDA graph"}
 
 
+def gi_loop(T, wl, xyz, w, params, veff, psi0, tol_gi=1e-5, max_iter=80):
+    """Green Iteration to tol_gi from the seeded start on one tree (Algorithm
+    2), with Anderson mixing of eigenpairs (beta 0.5, 5 past pairs) and
+    without; wall-clock seconds per loop, steps, and convolved orbital-steps."""
+    import torch
+
+    out = {"tol_gi": tol_gi, "max_iter": max_iter, "beta": 0.5, "history": 5}
+    h = T.tagi_tree_build(xyz, w, params)
+    try:
+        for name, kw in (("mixed", {}), ("plain", {"mix_tol": 0.0})):
+            psi = psi0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                r = T.tagi_green_iterate(h, veff, wl.vshift, psi, wl.eps, tol_gi, max_iter, **kw)
+            except T.TagiError as e:
+                out[name] = {"error": str(e)}
+                continue
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out[name] = {"s": dt, "steps": r["steps"], "converged": r["n_converged"],
+                         "field_steps": r["field_steps"], "iters": [int(x) for x in r["iters"]],
+                         "eps": [float(x) for x in r["eps"]], "ms_per_step": 1e3 * dt / max(1, r["steps"])}
+    finally:
+        T.tagi_tree_destroy(h)
+    return out
+
+
 def profile_case(args):
     """One tree and two Green steps, nothing else: the command ncu wraps."""
     import torch
@@ -400,6 +429,9 @@ def main():
     # ---- Green iterations replayed from a captured CUDA graph (fixed tree)
     graph = graph_replay(T, args, wl, xyz, w, params, veff, rho, vh, psi0, flush, inter, dev) if rank == 0 else None
 
+    # ---- Green Iteration to convergence (fixed V_eff), with and without mixing
+    loop = gi_loop(T, wl, xyz, w, params, veff, psi0) if (rank == 0 and not args.no_loop) else None
+
     # ---- end to end through the public API: pinned host inputs -> device,
     # step, results -> host, all inside the timed region
     hx = torch.tensor(wl.mesh.xyz).pin_memory()
@@ -489,6 +521,7 @@ def main():
                 "s_per_step": e2e_s},
         "gpu_launches": launches,
         "graph_replay": graph,
+        "green_iteration_loop": loop,
         "plain_fp64": plain,
         "cpu_baseline": cpu,
     }

@@ -245,6 +245,49 @@ tagi_status tagi_green_graph_launch(tagi_green_graph* graph, void* stream);
 tagi_status tagi_green_graph_check(tagi_green_graph* graph, void* stream);
 tagi_status tagi_green_graph_destroy(tagi_green_graph* graph);
 
+/* Green Iteration to convergence (Algorithm 2) for nw orbitals at once, with
+ * Anderson mixing of the eigenpairs x = (eps, psi) under the inner product
+ * (x1, x2) = eps1 eps2 + sum psi1 psi2 w (Section 4.3, "Wavefunction Mixing").
+ * Each step applies, to every orbital not yet converged, the Green step of
+ * tagi_green_step (G(eps) psi, the gradient-free eigenvalue update, then
+ * modified Gram-Schmidt in index order against every lower-index orbital --
+ * the new iterate of an active one, the stored pair of a converged one -- and
+ * normalisation), giving g(x) = (eps', psi') and the residual
+ * r = ||psi' - psi||_w (Algorithm 2 line 7).  Then:
+ *   r < tol_gi: the orbital is converged and keeps the input of that step,
+ *     (eps^(n), psi^(n)), as Algorithm 2 stores it; it is not convolved again;
+ *   else, before mixing starts: x <- g(x);
+ *   else (mixing, which starts once r < mix_tol and stays on): Anderson update
+ *     of the last history+1 pairs (x_j, F_j = g(x_j) - x_j): with
+ *     D_j = F_n - F_{n-j}, theta solves the normal equations of
+ *     min ||F_n - sum_j theta_j D_j||, and
+ *     x <- x_n - sum theta_j (x_n - x_{n-j}) + beta (F_n - sum theta_j D_j).
+ *     A Gram matrix with a pivot below 1e-13 of its largest diagonal entry
+ *     takes theta = 0 (simple mixing) for that step.
+ * The loop ends when every orbital has converged or after max_iter steps.
+ *   veff [dev] n; psi [dev] nw*n in/out; eps [host] nw in/out (unshifted);
+ *   resid [host] nw or NULL: each orbital's last residual;
+ *   iters [host] nw or NULL: the step at which each orbital converged, -1 if
+ *     it did not;  stats [host] or NULL.
+ * Errors: TAGI_ERR_INVALID_ARG for bad parameters, or when eps_o + vshift >= 0
+ * at the start or at any step (no decay, Section 3.3); psi and eps then hold
+ * the last completed step.  Synchronises the stream once per step. */
+typedef struct {
+    double tol_gi;   /* convergence tolerance, >= 0 */
+    int max_iter;    /* >= 1 */
+    double beta;     /* mixing parameter, in (0, 1]; the paper uses 0.5 */
+    int history;     /* 0..8 past pairs besides the newest (0: simple mixing) */
+    double mix_tol;  /* mixing starts once r < mix_tol (INFINITY: at once; 0: never) */
+} tagi_gi_params;
+typedef struct {
+    int steps;            /* Green steps taken */
+    int n_converged;      /* orbitals converged */
+    int64_t field_steps;  /* sum over steps of the orbitals convolved */
+} tagi_gi_stats;
+tagi_status tagi_green_iterate(tagi_tree* tree, const double* veff, double vshift, double* psi, double* eps,
+                               int nw, const tagi_gi_params* gp, double* resid, int* iters, tagi_gi_stats* stats,
+                               void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* tagi_last_error(void);
 

@@ -304,7 +304,8 @@ def green_iterate(tree, theta, degree, w, veff, vshift, psi, eps, tol_gi, max_it
 
     Returns psi, eps, resid (last residual per orbital), iters (the step count
     at which each orbital converged, -1 if it did not), steps, field_steps
-    (sum over steps of the orbitals convolved).
+    (sum over steps of the orbitals convolved) and trace (per step, the
+    residual of every orbital convolved in it, NaN for the others).
     """
     psi = np.array(np.atleast_2d(psi), np.float64)
     eps = np.array(eps, np.float64)
@@ -318,6 +319,7 @@ def green_iterate(tree, theta, degree, w, veff, vshift, psi, eps, tol_gi, max_it
     hx = [[] for _ in range(nw)]
     hf = [[] for _ in range(nw)]
     steps = field_steps = 0
+    trace = []
     for step in range(max_iter):
         act = np.flatnonzero(~conv)
         if act.size == 0:
@@ -338,9 +340,11 @@ def green_iterate(tree, theta, degree, w, veff, vshift, psi, eps, tol_gi, max_it
                 b = q[p] if p in q else psi[p]
                 v -= np.sum(v * b * w) * b
             q[o] = v / np.sqrt(np.sum(v * v * w))
+        trace.append(np.full(nw, np.nan))
         for o in act:
             f_psi = q[o] - psi[o]
             resid[o] = np.sqrt(np.sum(f_psi * f_psi * w))
+            trace[-1][o] = resid[o]
             if resid[o] < tol_gi:
                 conv[o] = True
                 iters[o] = step + 1
@@ -356,4 +360,5 @@ def green_iterate(tree, theta, degree, w, veff, vshift, psi, eps, tol_gi, max_it
                 eps[o], psi[o] = x[0], x[1:]
             else:
                 eps[o], psi[o] = e_new[o], q[o]
-    return {"psi": psi, "eps": eps, "resid": resid, "iters": iters, "steps": steps, "field_steps": field_steps}
+    return {"psi": psi, "eps": eps, "resid": resid, "iters": iters, "steps": steps, "field_steps": field_steps,
+            "trace": np.array(trace)}

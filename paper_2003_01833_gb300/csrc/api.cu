@@ -106,6 +106,8 @@ void ensure_part(Tree& T, int nf)
     T.part.ensure(sizeof(double) * (size_t)T.nitems * nf * kTargetsPerItem);
 }
 
+}  // namespace
+
 // Convolutions of nf caller-order rows f (device): rates from R (and eps_dev
 // for the first R.n_eps fields), outputs out[o].  Enqueued on T.stream, no
 // host synchronisation.
@@ -159,6 +161,8 @@ int read_err(Tree& T)
     TAGI_CUDA(cudaStreamSynchronize(T.stream));
     return h;
 }
+
+namespace {
 
 // One Green iteration with every per-iteration value on the device (eps_dev,
 // resid_dev, eh_dev): the sequence a captured graph replays.
@@ -443,6 +447,31 @@ tagi_status tagi_green_step(tagi_tree* tree, const double* veff, double vshift, 
         if (resid)
             for (int o = 0; o < nw; o++) resid[o] = r[o];
         if (rho && eh) *eh = h;
+    });
+}
+
+tagi_status tagi_green_iterate(tagi_tree* tree, const double* veff, double vshift, double* psi, double* eps,
+                               int nw, const tagi_gi_params* gp, double* resid, int* iters, tagi_gi_stats* stats,
+                               void* stream)
+{
+    return guarded([&] {
+        Tree* T = as_tree(tree);
+        TAGI_REQUIRE(veff != nullptr && psi != nullptr && eps != nullptr && gp != nullptr,
+                     "veff, psi, eps or params is NULL");
+        TAGI_REQUIRE(nw >= 1 && nw <= kMaxCallFields, "nw must be in [1, 128]");
+        TAGI_REQUIRE(std::isfinite(vshift), "vshift must be finite");
+        TAGI_REQUIRE(std::isfinite(gp->tol_gi) && gp->tol_gi >= 0.0, "tol_gi must be finite and >= 0");
+        TAGI_REQUIRE(gp->max_iter >= 1, "max_iter must be >= 1");
+        TAGI_REQUIRE(gp->beta > 0.0 && gp->beta <= 1.0, "beta must be in (0, 1]");
+        TAGI_REQUIRE(gp->history >= 0 && gp->history <= 8, "history must be in [0, 8]");
+        TAGI_REQUIRE(gp->mix_tol >= 0.0, "mix_tol must be >= 0 (INFINITY allowed)");
+        for (int o = 0; o < nw; o++) {
+            const double es = eps[o] + vshift;
+            TAGI_REQUIRE(std::isfinite(es) && es < 0.0, "eps + vshift must be negative (Section 3.3)");
+        }
+        T->stream = (cudaStream_t)stream;
+        AllocStream as(T->stream);
+        green_iterate(*T, veff, vshift, psi, eps, nw, *gp, resid, iters, stats);
     });
 }
 

@@ -88,9 +88,6 @@ __global__ void k_epilogue(EpiFields E, const double* __restrict__ kvd, int nf_g
 }
 
 // ---------------------------------------------------------------- dots
-struct DotJob {
-    const double *x, *zx, *y, *zy;
-};
 constexpr int kDotMax = 16;
 struct DotJobs {
     DotJob j[kDotMax];
@@ -161,9 +158,9 @@ __global__ void k_normalize(double* y, int64_t n, const double* d)
     if (i < n) y[i] /= sqrt(d[0]);
 }
 
+}  // namespace
 
-
-void run_dots(Tree& T, const std::vector<DotJob>& jobs, double* out_dev)
+void weighted_dots(Tree& T, const std::vector<DotJob>& jobs, double* out_dev)
 {
     cudaStream_t s = T.stream;
     T.scratch.ensure(sizeof(double) * kDotMax * kRedBlocks);
@@ -176,8 +173,6 @@ void run_dots(Tree& T, const std::vector<DotJob>& jobs, double* out_dev)
         TAGI_LAUNCH_CHECK();
     }
 }
-
-}  // namespace
 
 void prepare_points32(Tree& T, const double* f, int nf)
 {
@@ -286,6 +281,22 @@ __global__ void k_half(const double* a, double* out)
 }
 }  // namespace
 
+// v <- v - <v, b_p>_w b_p for each basis vector in order (modified
+// Gram-Schmidt), then v <- v / ||v||_w.  scalar: one device double.
+void orthonormalize(Tree& T, double* v, const std::vector<const double*>& basis, double* scalar)
+{
+    cudaStream_t s = T.stream;
+    const int64_t n = T.n;
+    const int nb = nblocks(n, 256);
+    for (const double* b : basis) {
+        weighted_dots(T, {DotJob{v, nullptr, b, nullptr}}, scalar);
+        launch(k_axpy_dev, nb, 256, 0, s, b, v, n, (const double*)scalar);
+    }
+    weighted_dots(T, {DotJob{v, nullptr, v, nullptr}}, scalar);
+    launch(k_normalize, nb, 256, 0, s, v, n, (const double*)scalar);
+    TAGI_LAUNCH_CHECK();
+}
+
 // Green step reductions, all on the device and without host synchronisation:
 // eps_dev (unshifted) updated in place, resid_dev[o] = ||psi_new - psi_old||_w.
 void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, double* eps_dev,
@@ -293,7 +304,6 @@ void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, 
 {
     cudaStream_t s = T.stream;
     const int64_t n = T.n;
-    const int nb = nblocks(n, 256);
     // psi~ = -2 u (Eq. Yukawa)
     launch(k_scale, nblocks(n * nw, 256), 256, 0, s, u, n * nw, -2.0);
     TAGI_LAUNCH_CHECK();
@@ -306,24 +316,19 @@ void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, 
         jobs.push_back(DotJob{f + o * n, nullptr, psi + o * n, u + o * n});
         jobs.push_back(DotJob{u + o * n, nullptr, u + o * n, nullptr});
     }
-    run_dots(T, jobs, dots);
+    weighted_dots(T, jobs, dots);
     launch(k_eps_update_dev, 1, 64 * ((nw + 63) / 64), 0, s, eps_dev, (const double*)dots, nw);
     TAGI_LAUNCH_CHECK();
     // modified Gram-Schmidt in index order under <a, b>_w
+    std::vector<const double*> basis;
     for (int o = 0; o < nw; o++) {
-        double* v = u + o * n;
-        for (int p = 0; p < o; p++) {
-            run_dots(T, {DotJob{v, nullptr, u + p * n, nullptr}}, one);
-            launch(k_axpy_dev, nb, 256, 0, s, (const double*)(u + p * n), v, n, (const double*)one);
-        }
-        run_dots(T, {DotJob{v, nullptr, v, nullptr}}, one);
-        launch(k_normalize, nb, 256, 0, s, v, n, (const double*)one);
-        TAGI_LAUNCH_CHECK();
+        orthonormalize(T, u + o * n, basis, one);
+        basis.push_back(u + o * n);
     }
     // residual ||psi_new - psi_old||_w, then psi <- psi_new
     jobs.clear();
     for (int o = 0; o < nw; o++) jobs.push_back(DotJob{u + o * n, psi + o * n, u + o * n, psi + o * n});
-    run_dots(T, jobs, dots);
+    weighted_dots(T, jobs, dots);
     if (resid_dev) launch(k_sqrt_copy, 1, 64 * ((nw + 63) / 64), 0, s, (const double*)dots, resid_dev, nw);
     TAGI_CUDA(cudaMemcpyAsync(psi, u, sizeof(double) * n * nw, cudaMemcpyDeviceToDevice, s));
     TAGI_LAUNCH_CHECK();
@@ -333,7 +338,7 @@ void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, 
 void hartree_energy(Tree& T, const double* vh, const double* rho, double* eh_dev)
 {
     T.dots2.ensure(sizeof(double) * 8);
-    run_dots(T, {DotJob{vh, nullptr, rho, nullptr}}, T.dots2.as<double>());
+    weighted_dots(T, {DotJob{vh, nullptr, rho, nullptr}}, T.dots2.as<double>());
     launch(k_half, 1, 32, 0, T.stream, (const double*)T.dots2.as<double>(), eh_dev);
     TAGI_LAUNCH_CHECK();
 }

@@ -232,6 +232,26 @@ void form_fields(Tree& T, const double* veff, double vshift, const double* psi, 
 void green_reductions(Tree& T, const double* f, double* psi, double* u, int nw, double* eps_dev,
                       double* resid_dev);
 void hartree_energy(Tree& T, const double* vh, const double* rho, double* eh_dev);
+// Weighted inner products on the device, out[j] = sum_i (x - zx)_i (y - zy)_i w_i
+// with the tree's quadrature weights in the caller's order (zx, zy may be null);
+// a fixed two-stage summation order, so results are reproducible.
+struct DotJob {
+    const double *x, *zx, *y, *zy;
+};
+void weighted_dots(Tree& T, const std::vector<DotJob>& jobs, double* out_dev);
+// modified Gram-Schmidt of v against basis (in order) and normalisation
+void orthonormalize(Tree& T, double* v, const std::vector<const double*>& basis, double* scalar);
+// api.cu: the convolution sequence (rates, fields, anterpolation, near/far,
+// epilogue) of nf caller-order rows, enqueued on T.stream without host sync
+void run_convolution(Tree& T, const double* f, const RateSrc& R, const double* eps_dev, double* const* out);
+RateSrc host_rates(const Tree& T, int nf);
+void clear_err(Tree& T);
+int read_err(Tree& T);  // synchronises T.stream
+
+// iterate.cu: Green Iteration with Anderson mixing (tagi_green_iterate);
+// eps is host memory, psi device memory in the caller's order
+void green_iterate(Tree& T, const double* veff, double vshift, double* psi, double* eps, int nw,
+                   const tagi_gi_params& gp, double* resid, int* iters, tagi_gi_stats* stats);
 
 // sets the message tagi_last_error returns on this thread; returns status
 tagi_status report_error(tagi_status status, const char* msg);

@@ -12,6 +12,7 @@ library is missing raises immediately -- there is no fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -49,6 +50,15 @@ class tagi_tree_stats(ctypes.Structure):
                 ("n_proxies", ctypes.c_int32)]
 
 
+class tagi_gi_params(ctypes.Structure):
+    _fields_ = [("tol_gi", ctypes.c_double), ("max_iter", ctypes.c_int), ("beta", ctypes.c_double),
+                ("history", ctypes.c_int), ("mix_tol", ctypes.c_double)]
+
+
+class tagi_gi_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("n_converged", ctypes.c_int), ("field_steps", ctypes.c_int64)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -74,6 +84,9 @@ def lib():
         L.tagi_coulomb_conv.argtypes = [_vp, _vp, _vp, _vp]
         L.tagi_green_step.argtypes = [_vp, _vp, ctypes.c_double, _vp, _D, ctypes.c_int, _vp, _vp, _D, _D, _vp]
         L.tagi_kernel_launches.restype = ctypes.c_int64
+        L.tagi_green_iterate.argtypes = [_vp, _vp, ctypes.c_double, _vp, _D, ctypes.c_int,
+                                         ctypes.POINTER(tagi_gi_params), _D, _I32, ctypes.POINTER(tagi_gi_stats),
+                                         _vp]
         L.tagi_profile_enable.argtypes = [ctypes.c_int]
         L.tagi_fp32_bias.argtypes = [_D, _D, _vp]
         L.tagi_green_graph_create.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp,
@@ -244,6 +257,32 @@ def tagi_green_step(tree, veff, vshift, psi, eps, rho=None, vh=None, stream=None
                                  _dptr(rho, "rho"), _dptr(vh, "vh"), res.ctypes.data_as(_D),
                                  eh.ctypes.data_as(_D) if rho is not None else None, _stream(stream)))
     return ea, res, (float(eh[0]) if rho is not None else None)
+
+
+def tagi_green_iterate(tree, veff, vshift, psi, eps, tol_gi, max_iter, beta=0.5, history=5, mix_tol=math.inf,
+                       stream=None):
+    """Green Iteration with Anderson mixing of eigenpairs until every orbital's
+    residual is below tol_gi (or max_iter steps).  psi: (nw, n) float64 CUDA,
+    updated in place; eps: nw host floats.
+
+    Returns a dict: eps, resid, iters (step of convergence, -1 if none),
+    steps, n_converged, field_steps."""
+    nw = psi.shape[0] if psi.dim() == 2 else 1
+    n = _tree_n(tree)
+    if psi.numel() != nw * n or veff.numel() != n:
+        raise ValueError("psi must be (nw, n) and veff must have n elements")
+    ea, ep = _hd(np.atleast_1d(eps).copy())
+    if ea.size != nw:
+        raise ValueError("one eigenvalue per orbital")
+    res = np.full(nw, np.nan)
+    its = np.full(nw, -1, dtype=np.int32)
+    gp = tagi_gi_params(float(tol_gi), int(max_iter), float(beta), int(history), float(mix_tol))
+    st = tagi_gi_stats()
+    _check(lib().tagi_green_iterate(tree, _dptr(veff, "veff"), float(vshift), _dptr(psi, "psi"), ep, nw,
+                                    ctypes.byref(gp), res.ctypes.data_as(_D), its.ctypes.data_as(_I32),
+                                    ctypes.byref(st), _stream(stream)))
+    return {"eps": ea, "resid": res, "iters": its, "steps": st.steps, "n_converged": st.n_converged,
+            "field_steps": st.field_steps}
 
 
 PROFILE_GROUPS = {"build": 0, "anterp": 1, "interact": 2, "epilogue": 3, "reduce": 4}

@@ -56,3 +56,15 @@ def test_argument_validation_needs_no_gpu(lib):
     assert lib.tagi_tree_destroy(None) == T.TAGI_OK
     lib.tagi_yukawa_conv.argtypes = [ctypes.c_void_p] * 6
     assert lib.tagi_yukawa_conv(None, None, None, 1, None, None) == T.TAGI_ERR_INVALID_ARG
+
+
+def test_green_iterate_validation_needs_no_gpu(lib):
+    import paper_2003_01833_gb300.tagi as T
+
+    L = T.lib()
+    gp = T.tagi_gi_params(1e-6, 10, 0.5, 5, float("inf"))
+    eps = (ctypes.c_double * 1)(-0.5)
+    # no tree
+    assert L.tagi_green_iterate(None, None, 0.0, None, eps, 1, ctypes.byref(gp), None, None, None,
+                                None) == T.TAGI_ERR_INVALID_ARG
+    assert "NULL" in T.lib().tagi_last_error().decode()
