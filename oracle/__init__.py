@@ -362,3 +362,139 @@ def green_iterate(tree, theta, degree, w, veff, vshift, psi, eps, tol_gi, max_it
                 eps[o], psi[o] = e_new[o], q[o]
     return {"psi": psi, "eps": eps, "resid": resid, "iters": iters, "steps": steps, "field_steps": field_steps,
             "trace": np.array(trace)}
+
+
+# --------------------------------------------------------------------------
+# SCF step (Algorithm 1 lines 2-7): LDA exchange-correlation, Fermi-Dirac
+# occupations (Eq. Fermi, density-construction), Anderson density mixing and
+# the gradient-free total energy (Eq. total-energy-gradient-free)
+# --------------------------------------------------------------------------
+
+# Perdew-Zunger parametrisation of the Ceperley-Alder correlation energy,
+# spin-unpolarised: (gamma, beta1, beta2) for r_s >= 1, (A, B, C, D) below
+_PZ_GAMMA, _PZ_B1, _PZ_B2 = -0.1423, 1.0529, 0.3334
+_PZ_A, _PZ_B, _PZ_C, _PZ_D = 0.0311, -0.048, 0.0020, -0.0116
+
+
+def _rs(rho):
+    return (3.0 / (4.0 * np.pi * rho)) ** (1.0 / 3.0)
+
+
+def lda_exchange(rho):
+    """Slater exchange in r_s form: eps_x = -(3/(4 pi)) (9 pi/4)^(1/3) / r_s,
+    v_x = 4/3 eps_x; zero where rho <= 1e-30.  Returns (eps_x, v_x)."""
+    rho = np.asarray(rho, np.float64)
+    e = np.zeros_like(rho)
+    m = rho > 1e-30
+    e[m] = -(3.0 / (4.0 * np.pi)) * (9.0 * np.pi / 4.0) ** (1.0 / 3.0) / _rs(rho[m])
+    return e, 4.0 / 3.0 * e
+
+
+def lda_correlation(rho):
+    """Perdew-Zunger correlation energy per electron and potential
+    v_c = eps_c - (r_s/3) d eps_c / d r_s; zero where rho <= 1e-30."""
+    rho = np.asarray(rho, np.float64)
+    e = np.zeros_like(rho)
+    v = np.zeros_like(rho)
+    m = rho > 1e-30
+    rs = _rs(rho[m])
+    ec = np.empty_like(rs)
+    dec = np.empty_like(rs)  # d eps_c / d r_s
+    lo = rs >= 1.0
+    x = rs[lo]
+    den = 1.0 + _PZ_B1 * np.sqrt(x) + _PZ_B2 * x
+    ec[lo] = _PZ_GAMMA / den
+    dec[lo] = -_PZ_GAMMA * (0.5 * _PZ_B1 / np.sqrt(x) + _PZ_B2) / den**2
+    x = rs[~lo]
+    ec[~lo] = _PZ_A * np.log(x) + _PZ_B + _PZ_C * x * np.log(x) + _PZ_D * x
+    dec[~lo] = _PZ_A / x + _PZ_C * (np.log(x) + 1.0) + _PZ_D
+    e[m] = ec
+    v[m] = ec - rs / 3.0 * dec
+    return e, v
+
+
+def lda_xc(rho):
+    ex, vx = lda_exchange(rho)
+    ec, vc = lda_correlation(rho)
+    return ex + ec, vx + vc
+
+
+def fermi_level(eps, n_elec, kT):
+    """Fermi energy mu with 2 sum_i f(eps_i, mu) = N_e and
+    f = 1 / (e^{(eps - mu)/kT} + 1) (Eq. Fermi, density-construction), by
+    bisection to the resolution of float64.  Returns (mu, f)."""
+    import scipy.special
+
+    eps = np.asarray(eps, np.float64)
+    if not (0.0 < n_elec < 2.0 * eps.size and kT > 0.0):
+        raise ValueError("need 0 < N_e < 2 N_w and kT > 0")
+    occ = lambda mu: scipy.special.expit((mu - eps) / kT)
+    lo, hi = eps.min() - 60.0 * kT, eps.max() + 60.0 * kT
+    for _ in range(400):
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if 2.0 * np.sum(occ(mid)) < n_elec:
+            lo = mid
+        else:
+            hi = mid
+    mu = 0.5 * (lo + hi)
+    return mu, occ(mu)
+
+
+def tol_gi_schedule(step, first=3e-3, final=1e-5, ramp=4):
+    """tol_gi for SCF step `step` (Section 6): `first` on the first step, then
+    geometric steps down to `final` over the next `ramp` steps."""
+    if step <= 0:
+        return first
+    if step >= ramp:
+        return final
+    return first * (final / first) ** (step / ramp)
+
+
+def scf_potentials(tree, theta, degree, w, vext, rho, alpha=1.0):
+    """V_eff[rho] = V_ext + V_H[rho] + V_xc[rho] (Eq. effective-potential;
+    V_H by the treecode with SS) and the double-counting terms of the
+    gradient-free energy: E_H = 1/2 <V_H, rho>, E_xc = <eps_xc, rho>,
+    E_vxc = <V_xc, rho>, all quadrature sums."""
+    vh = treecode_coulomb(tree, theta, degree, rho, w, alpha=alpha, ss=True)
+    exc, vxc = lda_xc(rho)
+    return {"veff": vext + vh + vxc, "vh": vh, "vxc": vxc, "e_h": 0.5 * np.sum(vh * rho * w),
+            "e_xc": np.sum(exc * rho * w), "e_vxc": np.sum(vxc * rho * w)}
+
+
+def scf_step(tree, theta, degree, w, vext, rho_in, psi, eps, vshift, n_elec, kT, e_zz, tol_gi, max_iter,
+             mix, scf_beta=0.5, scf_history=5, gi_beta=0.5, gi_history=5, mix_tol=np.inf, alpha=1.0):
+    """One SCF iteration (Algorithm 1):
+      line 2: V_eff[rho_in] (scf_potentials);
+      line 3: eigenpairs by Green Iteration with Anderson mixing
+        (green_iterate), warm-started from (eps, psi); the orbitals are then
+        normalised in the quadrature norm;
+      line 4: mu and occupations f_i (fermi_level);
+      line 5: rho_out = 2 sum_i f_i psi_i^2 (Eq. density-construction);
+      line 6: residual ||rho_out - rho_in||_w;
+      line 7: rho_next by Anderson mixing of the density under
+        <a, b> = sum a b w, from the history `mix` (a dict with lists 'x' and
+        'f', updated in place; the last scf_history + 1 pairs are kept).
+    Energy, gradient-free (Eq. total-energy-gradient-free), with the
+    double-counting terms of rho_in (the density that built V_eff):
+      E = 2 sum f_i eps_i - E_H + E_xc - <V_xc, rho_in> + E_ZZ.
+    """
+    pot = scf_potentials(tree, theta, degree, w, vext, rho_in, alpha=alpha)
+    gi = green_iterate(tree, theta, degree, w, pot["veff"], vshift, psi, eps, tol_gi, max_iter, beta=gi_beta,
+                       history=gi_history, mix_tol=mix_tol)
+    psi = gi["psi"] / np.sqrt(np.sum(gi["psi"] ** 2 * w[None, :], axis=1))[:, None]
+    eps = gi["eps"]
+    mu, f = fermi_level(eps, n_elec, kT)
+    rho_out = 2.0 * np.sum(f[:, None] * psi**2, axis=0)
+    resid = np.sqrt(np.sum((rho_out - rho_in) ** 2 * w))
+    mix.setdefault("x", []).append(np.array(rho_in, np.float64))
+    mix.setdefault("f", []).append(rho_out - rho_in)
+    mix["x"] = mix["x"][-(scf_history + 1):]
+    mix["f"] = mix["f"][-(scf_history + 1):]
+    rho_next = anderson_mix(np.array(mix["x"]), np.array(mix["f"]), scf_beta, w)
+    e_band = 2.0 * np.sum(f * eps)
+    energy = {"band": e_band, "hartree": pot["e_h"], "xc": pot["e_xc"], "vxc": pot["e_vxc"], "zz": e_zz,
+              "total": e_band - pot["e_h"] + pot["e_xc"] - pot["e_vxc"] + e_zz}
+    return {"psi": psi, "eps": eps, "mu": mu, "occ": f, "rho_out": rho_out, "rho_next": rho_next, "resid": resid,
+            "energy": energy, "gi": gi, "vh": pot["vh"], "veff": pot["veff"]}

@@ -202,6 +202,16 @@ def v_ext(mol: Molecule, pts: np.ndarray) -> np.ndarray:
     return v
 
 
+def nuclear_repulsion(mol: Molecule) -> float:
+    """E_ZZ = 1/2 sum_{i != j} Z_i Z_j / |R_i - R_j| (Eq. electrostatics)."""
+    Z, R = mol.Z, mol.pos
+    e = 0.0
+    for i in range(len(Z)):
+        for j in range(i + 1, len(Z)):
+            e += Z[i] * Z[j] / float(np.linalg.norm(R[i] - R[j]))
+    return e
+
+
 def v_hartree0(mol: Molecule, pts: np.ndarray) -> np.ndarray:
     v = np.zeros(pts.shape[:-1])
     for s, R in zip(mol.symbols, mol.pos):
@@ -400,6 +410,9 @@ class Workload:
     leaf_size: int
     alpha: float = 1.0
     meta: dict = field(default_factory=dict)
+    vext: np.ndarray = None  # (N,) external potential, for SCF steps (atoms and molecules)
+    n_elec: float = 0.0      # number of electrons N_e
+    e_zz: float = 0.0        # nuclear repulsion (Eq. electrostatics)
 
     @property
     def n(self) -> int:
@@ -482,11 +495,12 @@ def lithium(seed: int = 1, tol_m: float = 3e-7, p: int = 4, half_width: float = 
     psi1 = radial_orbital("1s", 3.0, r)
     psi2 = radial_orbital("2s", 3.0, r) * _smooth_perturbation(rng, pts)
     rho = density0(mol, pts)
-    veff = v_ext(mol, pts) + v_hartree0(mol, pts) + lda_xc(rho)[1]
+    vx = v_ext(mol, pts)
+    veff = vx + v_hartree0(mol, pts) + lda_xc(rho)[1]
     eps = np.array([-1.9, -0.11]) + rng.uniform(-0.02, 0.02, size=2)
     return Workload(name="Li", mesh=mesh, veff=veff, psi=np.stack([psi1, psi2]), eps=eps,
                     rho=rho, vshift=-0.5, theta=0.7, degree=8, leaf_size=2000,
-                    meta={"seed": seed, "tol_m": tol_m})
+                    meta={"seed": seed, "tol_m": tol_m}, vext=vx, n_elec=3.0, e_zz=0.0)
 
 
 def carbon_monoxide(seed: int = 2, tol_m: float = 3e-6, p: int = 4, half_width: float = 20.0,
@@ -527,10 +541,12 @@ def _molecule_workload(name, mol, mesh, seed, n_orb):
     coef = rng.normal(size=(n_orb, basis.shape[0]))
     psi = coef @ basis
     rho = density0(mol, pts)
-    veff = v_ext(mol, pts) + v_hartree0(mol, pts) + lda_xc(rho)[1]
+    vx = v_ext(mol, pts)
+    veff = vx + v_hartree0(mol, pts) + lda_xc(rho)[1]
     eps = np.sort(rng.uniform(-20.0, -0.3, size=n_orb))
     return Workload(name=name, mesh=mesh, veff=veff, psi=psi, eps=eps, rho=rho, vshift=-0.5,
-                    theta=0.7, degree=8, leaf_size=2000, meta={"seed": seed, "n_orb": n_orb})
+                    theta=0.7, degree=8, leaf_size=2000, meta={"seed": seed, "n_orb": n_orb}, vext=vx,
+                    n_elec=float(sum(ATOM_Z[a] for a in mol.symbols)), e_zz=nuclear_repulsion(mol))
 
 
 def random_cube(n: int, seed: int = 0, half_width: float = 1.0):
