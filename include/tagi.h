@@ -288,6 +288,63 @@ tagi_status tagi_green_iterate(tagi_tree* tree, const double* veff, double vshif
                                int nw, const tagi_gi_params* gp, double* resid, int* iters, tagi_gi_stats* stats,
                                void* stream);
 
+/* One SCF iteration (Algorithm 1 lines 2-7) on a fixed mesh (the tree):
+ *   line 2: V_eff = V_ext + V_H[rho_in] + V_xc[rho_in] (Eq. effective-potential;
+ *           V_H by the treecode Coulomb sum with SS, V_xc the spin-unpolarised
+ *           LDA of Section 2: Slater exchange, Perdew-Zunger correlation,
+ *           zero where rho <= 1e-30);
+ *   line 3: eigenpairs by tagi_green_iterate, warm-started from (eps, psi),
+ *           with tol_gi from the schedule below; then each psi_i is
+ *           normalised, sum psi_i^2 w = 1;
+ *   line 4: Fermi energy mu with 2 sum f_i = N_e, f_i = 1/(e^{(eps_i - mu)/kT} + 1)
+ *           (Eq. Fermi), by bisection to the resolution of float64;
+ *   line 5: rho_out = 2 sum f_i psi_i^2 (Eq. density-construction);
+ *   line 6: residual ||rho_out - rho_in||_w;
+ *   line 7: rho_next by Anderson mixing of the density under <a, b> = sum a b w
+ *           (tagi_green_iterate's update without the eigenvalue component),
+ *           from the pairs (rho_in, rho_out - rho_in) of this and earlier steps.
+ * Energy, gradient-free (Eq. total-energy-gradient-free), double-counting
+ * terms from rho_in:  E = 2 sum f_i eps_i - E_H + E_xc - <V_xc, rho_in> + E_ZZ,
+ * E_H = 1/2 <V_H, rho_in>, E_xc = <eps_xc, rho_in>.
+ * tol_gi schedule (Section 6): tol_gi_first on SCF step 0, then geometric
+ * steps to tol_gi_final over the next tol_gi_ramp steps, then tol_gi_final.
+ * Green Iteration mixing starts at once from step 1 on; on step 0 it starts
+ * once an orbital's residual is below gi_mix_tol_first (Section 4.3).
+ * The tagi_scf object keeps the density-mixing history and the step count;
+ * it refers to the tree, which must outlive it. */
+typedef struct {
+    double n_electrons;     /* N_e, 0 < N_e < 2 nw */
+    double kT;              /* k_B T in Ha, > 0 (Section 6: T = 200 K) */
+    double e_zz;            /* nuclear repulsion E_ZZ (Eq. electrostatics) */
+    double beta;            /* density mixing parameter, in (0, 1] */
+    int history;            /* density mixing depth, 0..8 */
+    double tol_gi_first;    /* > 0 */
+    double tol_gi_final;    /* > 0 */
+    int tol_gi_ramp;        /* >= 0 */
+    int gi_max_iter;        /* >= 1 */
+    double gi_beta;         /* eigenpair mixing parameter, in (0, 1] */
+    int gi_history;         /* 0..8 */
+    double gi_mix_tol_first;/* >= 0, INFINITY allowed */
+} tagi_scf_params;
+typedef struct {
+    int step;               /* index of the SCF step just taken (0-based) */
+    double tol_gi;          /* Green Iteration tolerance it used */
+    double mu;              /* Fermi energy */
+    double residual;        /* ||rho_out - rho_in||_w */
+    double e_band, e_hartree, e_xc, e_vxc, e_zz, e_total;
+    tagi_gi_stats gi;       /* the Green Iteration of this step */
+} tagi_scf_report;
+typedef struct tagi_scf tagi_scf;
+tagi_status tagi_scf_create(tagi_tree* tree, const tagi_scf_params* params, tagi_scf** out);
+/*   vext [dev] n; rho [dev] n, in: rho_in, out: rho_next; psi [dev] nw*n in/out;
+ *   eps [host] nw in/out (unshifted); occ [host] nw out or NULL;
+ *   rho_out [dev] n out or NULL; report [host] or NULL.
+ * Errors: as tagi_green_iterate, and TAGI_ERR_INVALID_ARG for N_e outside
+ * (0, 2 nw).  Synchronises the stream. */
+tagi_status tagi_scf_step(tagi_scf* scf, const double* vext, double vshift, double* rho, double* psi, double* eps,
+                          int nw, double* occ, double* rho_out, tagi_scf_report* report, void* stream);
+tagi_status tagi_scf_destroy(tagi_scf* scf);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* tagi_last_error(void);
 

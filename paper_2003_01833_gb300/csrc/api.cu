@@ -475,6 +475,59 @@ tagi_status tagi_green_iterate(tagi_tree* tree, const double* veff, double vshif
     });
 }
 
+tagi_status tagi_scf_create(tagi_tree* tree, const tagi_scf_params* p, tagi_scf** out)
+{
+    return guarded([&] {
+        TAGI_REQUIRE(out != nullptr && p != nullptr, "params or out is NULL");
+        *out = nullptr;
+        Tree* T = as_tree(tree);
+        TAGI_REQUIRE(std::isfinite(p->n_electrons) && p->n_electrons > 0.0, "n_electrons must be > 0");
+        TAGI_REQUIRE(std::isfinite(p->kT) && p->kT > 0.0, "kT must be > 0");
+        TAGI_REQUIRE(std::isfinite(p->e_zz), "e_zz must be finite");
+        TAGI_REQUIRE(p->beta > 0.0 && p->beta <= 1.0, "beta must be in (0, 1]");
+        TAGI_REQUIRE(p->history >= 0 && p->history <= 8, "history must be in [0, 8]");
+        TAGI_REQUIRE(std::isfinite(p->tol_gi_first) && p->tol_gi_first > 0.0 && std::isfinite(p->tol_gi_final) &&
+                         p->tol_gi_final > 0.0 && p->tol_gi_ramp >= 0,
+                     "tol_gi schedule must be positive");
+        TAGI_REQUIRE(p->gi_max_iter >= 1, "gi_max_iter must be >= 1");
+        TAGI_REQUIRE(p->gi_beta > 0.0 && p->gi_beta <= 1.0, "gi_beta must be in (0, 1]");
+        TAGI_REQUIRE(p->gi_history >= 0 && p->gi_history <= 8, "gi_history must be in [0, 8]");
+        TAGI_REQUIRE(p->gi_mix_tol_first >= 0.0, "gi_mix_tol_first must be >= 0");
+        *out = reinterpret_cast<tagi_scf*>(new Scf(T, *p));
+    });
+}
+
+tagi_status tagi_scf_step(tagi_scf* scf, const double* vext, double vshift, double* rho, double* psi, double* eps,
+                          int nw, double* occ, double* rho_out, tagi_scf_report* report, void* stream)
+{
+    return guarded([&] {
+        TAGI_REQUIRE(scf != nullptr, "scf is NULL");
+        Scf* S = reinterpret_cast<Scf*>(scf);
+        TAGI_REQUIRE(vext != nullptr && rho != nullptr && psi != nullptr && eps != nullptr,
+                     "vext, rho, psi or eps is NULL");
+        TAGI_REQUIRE(nw >= 1 && nw <= kMaxCallFields, "nw must be in [1, 128]");
+        TAGI_REQUIRE(S->p.n_electrons < 2.0 * nw, "n_electrons must be below 2 nw");
+        TAGI_REQUIRE(std::isfinite(vshift), "vshift must be finite");
+        for (int o = 0; o < nw; o++) {
+            const double es = eps[o] + vshift;
+            TAGI_REQUIRE(std::isfinite(es) && es < 0.0, "eps + vshift must be negative (Section 3.3)");
+        }
+        S->T->stream = (cudaStream_t)stream;
+        AllocStream as(S->T->stream);
+        scf_step(*S, vext, vshift, rho, psi, eps, nw, occ, rho_out, report);
+    });
+}
+
+tagi_status tagi_scf_destroy(tagi_scf* scf)
+{
+    return guarded([&] {
+        if (!scf) return;
+        Scf* S = reinterpret_cast<Scf*>(scf);
+        TAGI_CUDA(cudaDeviceSynchronize());
+        delete S;
+    });
+}
+
 tagi_status tagi_green_graph_create(tagi_tree* tree, const double* veff, double vshift, double* psi, double* eps,
                                     int nw, const double* rho, double* vh, double* resid, double* eh, void* stream,
                                     tagi_green_graph** out)

@@ -8,6 +8,7 @@
 // inner products, with the eps component added in the solve.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -149,6 +150,98 @@ __global__ void k_anderson_combine(Rows R, int m, double beta, const double* __r
     double s = 0.0;
     for (int j = 0; j <= m; j++) s += coef[j] * (R.x[j][i] + beta * R.f[j][i]);
     out[i] = s;
+}
+
+// ---------------------------------------------------------------- SCF kernels
+// Spin-unpolarised LDA (Section 2): Slater exchange
+//   eps_x = -(3/4) (3 rho/pi)^(1/3), v_x = -(3 rho/pi)^(1/3),
+// and the Perdew-Zunger fit of the Ceperley-Alder correlation in
+// r_s = (3/(4 pi rho))^(1/3): for r_s >= 1
+//   eps_c = g/(1 + b1 sqrt(r_s) + b2 r_s), v_c = eps_c (1 + 7/6 b1 sqrt(r_s) + 4/3 b2 r_s)/(1 + b1 sqrt(r_s) + b2 r_s),
+// below it eps_c = A ln r_s + B + C r_s ln r_s + D r_s,
+//   v_c = A ln r_s + (B - A/3) + 2/3 C r_s ln r_s + (2D - C)/3 r_s.
+__global__ void k_lda(const double* __restrict__ rho, int64_t n, double* __restrict__ exc, double* __restrict__ vxc)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r = rho[i];
+    if (!(r > 1e-30)) {
+        exc[i] = 0.0;
+        vxc[i] = 0.0;
+        return;
+    }
+    const double kPi = 3.14159265358979323846;
+    const double t = cbrt(3.0 * r / kPi);
+    double e = -0.75 * t, v = -t;
+    const double rs = cbrt(3.0 / (4.0 * kPi * r));
+    if (rs >= 1.0) {
+        const double g = -0.1423, b1 = 1.0529, b2 = 0.3334;
+        const double sq = sqrt(rs), den = 1.0 + b1 * sq + b2 * rs;
+        const double ec = g / den;
+        e += ec;
+        v += ec * (1.0 + 7.0 / 6.0 * b1 * sq + 4.0 / 3.0 * b2 * rs) / den;
+    } else {
+        const double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
+        const double ln = log(rs);
+        e += A * ln + B + C * rs * ln + D * rs;
+        v += A * ln + (B - A / 3.0) + 2.0 / 3.0 * C * rs * ln + (2.0 * D - C) / 3.0 * rs;
+    }
+    exc[i] = e;
+    vxc[i] = v;
+}
+
+__global__ void k_add3(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ c,
+                       int64_t n, double* __restrict__ out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] + b[i] + c[i];
+}
+
+// Fermi energy by bisection (one thread): 2 sum_i f(eps_i, mu) = N_e,
+// f = 1/(1 + e^{(eps - mu)/kT}).  out: mu, band energy 2 sum f eps.
+__global__ void k_fermi(const double* __restrict__ eps, int nw, double ne, double kT, double* __restrict__ f,
+                        double* __restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double lo = eps[0], hi = eps[0];
+    for (int o = 1; o < nw; o++) {
+        lo = fmin(lo, eps[o]);
+        hi = fmax(hi, eps[o]);
+    }
+    lo -= 60.0 * kT;
+    hi += 60.0 * kT;
+    for (int it = 0; it < 400; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double s = 0.0;
+        for (int o = 0; o < nw; o++) s += 1.0 / (1.0 + exp((eps[o] - mid) / kT));
+        if (2.0 * s < ne)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const double mu = 0.5 * (lo + hi);
+    double band = 0.0;
+    for (int o = 0; o < nw; o++) {
+        f[o] = 1.0 / (1.0 + exp((eps[o] - mu) / kT));
+        band += 2.0 * f[o] * eps[o];
+    }
+    out[0] = mu;
+    out[1] = band;
+}
+
+// rho_out = 2 sum_o f_o psi_o^2
+__global__ void k_density(const double* __restrict__ psi, const double* __restrict__ f, int nw, int64_t n,
+                          double* __restrict__ rho)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int o = 0; o < nw; o++) {
+        const double p = psi[(size_t)o * n + i];
+        s += f[o] * p * p;
+    }
+    rho[i] = 2.0 * s;
 }
 
 }  // namespace
@@ -318,6 +411,130 @@ void green_iterate(Tree& T, const double* veff, double vshift, double* psi, doub
         stats->n_converged = nconv;
         stats->field_steps = field_steps;
     }
+}
+
+// ---------------------------------------------------------------- SCF step
+Scf::Scf(Tree* t, const tagi_scf_params& prm) : T(t), p(prm) {}
+
+void scf_step(Scf& S, const double* vext, double vshift, double* rho, double* psi, double* eps, int nw,
+              double* occ, double* rho_out_user, tagi_scf_report* rep)
+{
+    Tree& T = *S.T;
+    cudaStream_t s = T.stream;
+    const int64_t n = T.n;
+    const int nb = nblocks(n, 256);
+    const int ring = S.p.history + 1;
+    DevBuf vh, exc, vxc, veff, rho_out, fo, scal, zero, coef;
+    vh.ensure(sizeof(double) * n);
+    exc.ensure(sizeof(double) * n);
+    vxc.ensure(sizeof(double) * n);
+    veff.ensure(sizeof(double) * n);
+    rho_out.ensure(sizeof(double) * n);
+    fo.ensure(sizeof(double) * (nw + 1));
+    scal.ensure(sizeof(double) * 16);
+    zero.ensure(sizeof(double) * 2);
+    coef.ensure(sizeof(double) * (kMaxHist + 1) * 2);
+    TAGI_CUDA(cudaMemsetAsync(zero.p, 0, sizeof(double) * 2, s));
+    double* sc = scal.as<double>();  // [0] mu [1] band [2..4] E_H, E_xc, E_vxc [5] resid^2 [8] scratch
+
+    // line 2: V_eff[rho_in]
+    {
+        RateSrc R = host_rates(T, 1);
+        R.kind[0] = 1;
+        R.val[0] = T.alpha;
+        double* out = vh.as<double>();
+        clear_err(T);
+        run_convolution(T, rho, R, nullptr, &out);
+    }
+    launch(k_lda, nb, 256, 0, s, (const double*)rho, n, exc.as<double>(), vxc.as<double>());
+    launch(k_add3, nb, 256, 0, s, vext, (const double*)vh.p, (const double*)vxc.p, n, veff.as<double>());
+    TAGI_LAUNCH_CHECK();
+    // double-counting terms of the energy, from rho_in
+    weighted_dots(T, {DotJob{vh.as<double>(), nullptr, rho, nullptr}, DotJob{exc.as<double>(), nullptr, rho, nullptr},
+                      DotJob{vxc.as<double>(), nullptr, rho, nullptr}},
+                  sc + 2);
+
+    // line 3: eigenpairs by Green Iteration
+    const int k = S.step;
+    double tol = S.p.tol_gi_final;
+    if (k <= 0)
+        tol = S.p.tol_gi_first;
+    else if (k < S.p.tol_gi_ramp)
+        tol = S.p.tol_gi_first * std::pow(S.p.tol_gi_final / S.p.tol_gi_first, (double)k / S.p.tol_gi_ramp);
+    tagi_gi_params gp{tol, S.p.gi_max_iter, S.p.gi_beta, S.p.gi_history,
+                      k == 0 ? S.p.gi_mix_tol_first : (double)INFINITY};
+    tagi_gi_stats gst{};
+    green_iterate(T, veff.as<double>(), vshift, psi, eps, nw, gp, nullptr, nullptr, &gst);
+    for (int o = 0; o < nw; o++) orthonormalize(T, psi + (size_t)o * n, {}, sc + 8);
+
+    // line 4: occupations; line 5: density
+    TAGI_CUDA(cudaMemcpyAsync(fo.p, eps, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
+    DevBuf fv;
+    fv.ensure(sizeof(double) * nw);
+    launch(k_fermi, 1, 32, 0, s, (const double*)fo.p, nw, S.p.n_electrons, S.p.kT, fv.as<double>(), sc);
+    launch(k_density, nb, 256, 0, s, (const double*)psi, (const double*)fv.p, nw, n, rho_out.as<double>());
+    TAGI_LAUNCH_CHECK();
+    // line 6: residual
+    weighted_dots(T, {DotJob{rho_out.as<double>(), rho, rho_out.as<double>(), rho}}, sc + 5);
+    if (rho_out_user)
+        TAGI_CUDA(cudaMemcpyAsync(rho_out_user, rho_out.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+
+    // line 7: Anderson mixing of the density (no scalar component)
+    if (!S.hist.p) {
+        S.hist.ensure(sizeof(double) * (size_t)ring * 2 * n);
+        S.hring.ensure(sizeof(double) * (size_t)ring * 2);
+        TAGI_CUDA(cudaMemsetAsync(S.hring.p, 0, sizeof(double) * (size_t)ring * 2, s));
+    }
+    double* hx = S.hist.as<double>();
+    double* hf = hx + (size_t)ring * n;
+    double* hxe = S.hring.as<double>();
+    double* hfe = hxe + ring;
+    S.head = (S.head + 1) % ring;
+    S.count = std::min(S.count + 1, ring);
+    const int h = S.head;
+    launch(k_push, nb, 256, 0, s, (const double*)rho, (const double*)rho_out.p, n, hx + (size_t)h * n,
+           hf + (size_t)h * n, (const double*)zero.p, (const double*)zero.p, hxe + h, hfe + h);
+    MixArgs M{};
+    M.m = S.count - 1;
+    M.beta = S.p.beta;
+    Rows rows{};
+    for (int j = 0; j <= M.m; j++) {
+        M.slot[j] = (h - j + ring) % ring;
+        rows.x[j] = hx + (size_t)M.slot[j] * n;
+        rows.f[j] = hf + (size_t)M.slot[j] * n;
+    }
+    std::vector<DotJob> jobs;
+    for (int j = 1; j <= M.m; j++)
+        for (int l = j; l <= M.m; l++) jobs.push_back(DotJob{rows.f[0], rows.f[j], rows.f[0], rows.f[l]});
+    for (int j = 1; j <= M.m; j++) jobs.push_back(DotJob{rows.f[0], rows.f[j], rows.f[0], nullptr});
+    T.dots2.ensure(sizeof(double) * (kMaxHist * (kMaxHist + 3) / 2 + 8));
+    if (!jobs.empty()) weighted_dots(T, jobs, T.dots2.as<double>());
+    launch(k_anderson_solve, 1, 32, 0, s, M, (const double*)T.dots2.p, (const double*)hxe, (const double*)hfe,
+           coef.as<double>(), sc + 9);
+    launch(k_anderson_combine, nb, 256, 0, s, rows, M.m, S.p.beta, (const double*)coef.p, n, rho);
+    TAGI_LAUNCH_CHECK();
+
+    double hs[16];
+    std::vector<double> fh(nw);
+    TAGI_CUDA(cudaMemcpyAsync(hs, sc, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
+    TAGI_CUDA(cudaMemcpyAsync(fh.data(), fv.p, sizeof(double) * nw, cudaMemcpyDeviceToHost, s));
+    TAGI_CUDA(cudaStreamSynchronize(s));
+    if (occ)
+        for (int o = 0; o < nw; o++) occ[o] = fh[o];
+    if (rep) {
+        rep->step = k;
+        rep->tol_gi = tol;
+        rep->mu = hs[0];
+        rep->residual = std::sqrt(hs[5]);
+        rep->e_band = hs[1];
+        rep->e_hartree = 0.5 * hs[2];
+        rep->e_xc = hs[3];
+        rep->e_vxc = hs[4];
+        rep->e_zz = S.p.e_zz;
+        rep->e_total = rep->e_band - rep->e_hartree + rep->e_xc - rep->e_vxc + rep->e_zz;
+        rep->gi = gst;
+    }
+    S.step++;
 }
 
 }  // namespace tagi

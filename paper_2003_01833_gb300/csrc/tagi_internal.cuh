@@ -253,6 +253,17 @@ int read_err(Tree& T);  // synchronises T.stream
 void green_iterate(Tree& T, const double* veff, double vshift, double* psi, double* eps, int nw,
                    const tagi_gi_params& gp, double* resid, int* iters, tagi_gi_stats* stats);
 
+// SCF state (tagi_scf): parameters, step count, density-mixing history
+struct Scf {
+    Tree* T;
+    tagi_scf_params p;
+    int step = 0, count = 0, head = -1;
+    DevBuf hist, hring;
+    Scf(Tree* t, const tagi_scf_params& prm);
+};
+void scf_step(Scf& S, const double* vext, double vshift, double* rho, double* psi, double* eps, int nw,
+              double* occ, double* rho_out, tagi_scf_report* rep);
+
 // sets the message tagi_last_error returns on this thread; returns status
 tagi_status report_error(tagi_status status, const char* msg);
 

@@ -59,6 +59,20 @@ class tagi_gi_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("n_converged", ctypes.c_int), ("field_steps", ctypes.c_int64)]
 
 
+class tagi_scf_params(ctypes.Structure):
+    _fields_ = [("n_electrons", ctypes.c_double), ("kT", ctypes.c_double), ("e_zz", ctypes.c_double),
+                ("beta", ctypes.c_double), ("history", ctypes.c_int), ("tol_gi_first", ctypes.c_double),
+                ("tol_gi_final", ctypes.c_double), ("tol_gi_ramp", ctypes.c_int), ("gi_max_iter", ctypes.c_int),
+                ("gi_beta", ctypes.c_double), ("gi_history", ctypes.c_int), ("gi_mix_tol_first", ctypes.c_double)]
+
+
+class tagi_scf_report(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int), ("tol_gi", ctypes.c_double), ("mu", ctypes.c_double),
+                ("residual", ctypes.c_double), ("e_band", ctypes.c_double), ("e_hartree", ctypes.c_double),
+                ("e_xc", ctypes.c_double), ("e_vxc", ctypes.c_double), ("e_zz", ctypes.c_double),
+                ("e_total", ctypes.c_double), ("gi", tagi_gi_stats)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -87,6 +101,10 @@ def lib():
         L.tagi_green_iterate.argtypes = [_vp, _vp, ctypes.c_double, _vp, _D, ctypes.c_int,
                                          ctypes.POINTER(tagi_gi_params), _D, _I32, ctypes.POINTER(tagi_gi_stats),
                                          _vp]
+        L.tagi_scf_create.argtypes = [_vp, ctypes.POINTER(tagi_scf_params), ctypes.POINTER(_vp)]
+        L.tagi_scf_step.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp, _D, ctypes.c_int, _D, _vp,
+                                    ctypes.POINTER(tagi_scf_report), _vp]
+        L.tagi_scf_destroy.argtypes = [_vp]
         L.tagi_profile_enable.argtypes = [ctypes.c_int]
         L.tagi_fp32_bias.argtypes = [_D, _D, _vp]
         L.tagi_green_graph_create.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp,
@@ -283,6 +301,56 @@ def tagi_green_iterate(tree, veff, vshift, psi, eps, tol_gi, max_iter, beta=0.5,
                                     ctypes.byref(st), _stream(stream)))
     return {"eps": ea, "resid": res, "iters": its, "steps": st.steps, "n_converged": st.n_converged,
             "field_steps": st.field_steps}
+
+
+class Scf:
+    """SCF iteration state on one tree (tagi_scf_*): density-mixing history
+    and the tol_gi schedule.  Use as a context manager or call close()."""
+
+    def __init__(self, tree, n_electrons, kT=6.3336e-4, e_zz=0.0, beta=0.5, history=5, tol_gi_first=3e-3,
+                 tol_gi_final=1e-5, tol_gi_ramp=4, gi_max_iter=100, gi_beta=0.5, gi_history=5,
+                 gi_mix_tol_first=math.inf):
+        self.tree = tree
+        p = tagi_scf_params(float(n_electrons), float(kT), float(e_zz), float(beta), int(history),
+                            float(tol_gi_first), float(tol_gi_final), int(tol_gi_ramp), int(gi_max_iter),
+                            float(gi_beta), int(gi_history), float(gi_mix_tol_first))
+        h = _vp()
+        _check(lib().tagi_scf_create(tree, ctypes.byref(p), ctypes.byref(h)))
+        self.handle = h
+
+    def step(self, vext, vshift, rho, psi, eps, rho_out=None, stream=None):
+        """One SCF iteration: rho (n,) CUDA in: rho_in, out: the mixed next
+        input; psi (nw, n) CUDA in/out; eps nw host floats.  Returns a dict of
+        the report fields plus eps and occ (NumPy)."""
+        nw = psi.shape[0] if psi.dim() == 2 else 1
+        n = _tree_n(self.tree)
+        if psi.numel() != nw * n or vext.numel() != n or rho.numel() != n or (
+                rho_out is not None and rho_out.numel() != n):
+            raise ValueError("psi must be (nw, n); vext, rho and rho_out must have n elements")
+        ea, ep = _hd(np.atleast_1d(eps).copy())
+        if ea.size != nw:
+            raise ValueError("one eigenvalue per orbital")
+        occ = np.zeros(nw)
+        rep = tagi_scf_report()
+        _check(lib().tagi_scf_step(self.handle, _dptr(vext, "vext"), float(vshift), _dptr(rho, "rho"),
+                                   _dptr(psi, "psi"), ep, nw, occ.ctypes.data_as(_D), _dptr(rho_out, "rho_out"),
+                                   ctypes.byref(rep), _stream(stream)))
+        out = {f: getattr(rep, f) for f, _ in tagi_scf_report._fields_ if f != "gi"}
+        out["gi"] = {"steps": rep.gi.steps, "n_converged": rep.gi.n_converged, "field_steps": rep.gi.field_steps}
+        out["eps"] = ea
+        out["occ"] = occ
+        return out
+
+    def close(self):
+        if self.handle is not None:
+            _check(lib().tagi_scf_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 PROFILE_GROUPS = {"build": 0, "anterp": 1, "interact": 2, "epilogue": 3, "reduce": 4}
