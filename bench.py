@@ -139,33 +139,48 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ roofline model
-# Thread instructions issued per pair in the FP32C kernel, counted from the
-# source of tile_near / tile_far (FP32 pipe + MUFU; shared-memory loads, the
-# self-pair mask, the two-float folds and loop overhead excluded).
-# Near, per pair: difference 3, r^2 3, rsqrt 1, r 1, r (w_hi + w_lo) 2 -> 10;
-# per Yukawa field: k r 1, ex2 1, SS difference 2, e r w 1, accumulate 1 -> 6;
-# Hartree: a r^2 1, ex2 1, c g subtraction 1, + f_lo 1, accumulate 1 -> 5.
-# Far, per pair: difference 3, r^2 3, rsqrt 1, r 1 -> 8; per Yukawa field:
-# k r 1, ex2 1, q - c w 1, e / r 1, accumulate 1 -> 5; Hartree: a r^2 1,
-# ex2 1, c w 1, subtraction 1, accumulate 1 -> 5.
+# Thread instructions issued per pair in the FP32C kernel are counted from the
+# source of tile_near / tile_far / tile_far_tensor (FP32 pipe + MUFU;
+# shared-memory loads, the self-pair mask, the two-float folds and loop
+# overhead excluded), see kernel_work.
 ISSUE_PER_SM_CLK = 128  # 4 schedulers x 32 lanes, one warp instruction each per clock
+XU_EX2_PER_SM_CLK = 30.1  # measured ex2.approx rate per SM per clock on the GB300; rsqrt.approx runs at half
 
 
-def issue_per_pair(ny, hh):
-    near = 10 + 6 * ny + (5 if hh else 0)
-    far = 8 + 5 * ny + (5 if hh else 0)
-    return near, far
+def kernel_work(info, ny, hh):
+    """Work of one k_interact32 launch, summed over its pairs: FP32-pipe plus
+    MUFU instructions per pair as counted from the kernel source, and MUFU
+    work in ex2 units (rsqrt = 2).  Per pair:
+      near (record path): 10 geometry (3 differences, r^2 in 3, rsqrt, r,
+        r (w_hi + w_lo) in 2), 6 per Yukawa field, 5 for the Hartree field
+        (2 where the entry leaves out the Gaussian, list flag bit2);
+      far: 4 geometry on the tensor grid (degrees 6 and 8: one difference, one
+        FMA, rsqrt, r), else 8; 5 per Yukawa field; Hartree 5 (1 without
+        the Gaussian)."""
+    tensor = info["degree"] in (6, 8)
+    nn, nfar = info["near_pairs"], info["far_pairs"]
+    nng, nfg = (info["near_pairs_nogauss"], info["far_pairs_nogauss"]) if hh else (0, 0)
+    near_g, near_ng = 10 + 6 * ny + (5 if hh else 0), 10 + 6 * ny + (2 if hh else 0)
+    geo = 4 if tensor else 8
+    far_g, far_ng = geo + 5 * ny + (5 if hh else 0), geo + 5 * ny + (1 if hh else 0)
+    instr = (nn - nng) * near_g + nng * near_ng + (nfar - nfg) * far_g + nfg * far_ng
+    xu = (nn + nfar) * (2 + ny) + ((nn - nng) + (nfar - nfg)) * (1 if hh else 0)
+    return instr, xu
 
 
 def roofline(info, nfields_y, hh, kernel_ms, clk_mhz, sms):
-    near, far = issue_per_pair(nfields_y, hh)
+    """ALU roofline of k_interact32: the tighter of the issue bound (128
+    instructions per SM per clock) and the MUFU bound (measured ex2 rate)."""
+    instr, xu = kernel_work(info, nfields_y, hh)
     nf = nfields_y + (1 if hh else 0)
-    instr = info["near_pairs"] * near + info["far_pairs"] * far
     inter = (info["near_pairs"] + info["far_pairs"]) * nf
-    per_inter = instr / inter
-    peak = sms * ISSUE_PER_SM_CLK * clk_mhz * 1e6 / per_inter  # interactions/s
+    f = clk_mhz * 1e6
+    peak_issue = sms * ISSUE_PER_SM_CLK * f * inter / instr
+    peak_xu = sms * XU_EX2_PER_SM_CLK * f * inter / xu
     achieved = inter / (kernel_ms * 1e-3)
-    return achieved, peak, per_inter
+    return achieved, min(peak_issue, peak_xu), {"issue_bound": peak_issue, "mufu_bound": peak_xu,
+                                                "instr_per_interaction": instr / inter,
+                                                "mufu_ex2_units_per_interaction": xu / inter}
 
 
 # ------------------------------------------------------------------ oracle legs
@@ -539,7 +554,7 @@ def main():
     k_ms, k_cnt = prof["interact"]
     k_ms_per_step = k_ms / max(1, args.steps)
     clk_mhz = clk.get("sm_mhz") or 1900.0
-    achieved, peak, per_inter = roofline(info, nw, True, k_ms_per_step, clk_mhz, sms)
+    achieved, peak, bounds = roofline(info, nw, True, k_ms_per_step, clk_mhz, sms)
     cpu = None
     if not args.no_cpu:
         rate, threads, desc, _ = cpu_oracle_rate(wl, budget_s=20.0)
@@ -558,9 +573,11 @@ def main():
         "phases_ms_per_step": {g: prof[g][0] / max(1, args.steps) for g in prof},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "interactions/s",
                      "frac": achieved / peak, "traffic": kernel_traffic(),
-                     "kernel": "k_interact32 (near/far)", "issue_per_interaction": per_inter,
-                     "peak_model": f"{sms} SMs x 128 issue/clk x {clk_mhz:.0f} MHz / {per_inter:.2f} instr per "
-                                   "interaction (measured clock)"},
+                     "kernel": "k_interact32 (near/far)", **bounds,
+                     "peak_model": f"min(issue: {sms} SMs x 128 instr/clk, MUFU: {sms} SMs x "
+                                   f"{XU_EX2_PER_SM_CLK} ex2/clk) x {clk_mhz:.0f} MHz (measured clock) over the "
+                                   "per-interaction counts; peak of measured unit rates, not MEASURED_PEAKS.json "
+                                   "(HBM and bf16 tensor peaks do not bound this kernel)"},
         "clocks": clk,
         "e2e": {"value": inter_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "s_per_step": e2e_s},

@@ -25,10 +25,16 @@
 // epilogue.  Quadrature weights of mesh points are two-float too: adaptive
 // octree cells scale by powers of two, so a float32 rounding of w repeats the
 // same few relative errors everywhere and would bias sum_j G w_j, which the
-// singularity subtraction amplifies.  Every 8 sources the float32 partial sums are
-// folded into a per-target two-float (hi, lo) accumulator with an error-free
-// TwoSum.  The SS constant c_i is the float32 high part of f_i, the same value
+// singularity subtraction amplifies.  Every 16 sources (every row of proxies
+// on the tensor far path) the float32 partial sums are folded into a
+// per-target two-float (hi, lo) accumulator with an error-free TwoSum.  The SS constant c_i is the float32 high part of f_i, the same value
 // the epilogue uses, so the subtraction telescopes exactly.
+//
+// Approximated clusters of degree 6 or 8 take the tensor-grid far path
+// (tile_far_tensor): proxies sit on a product grid, so the squared distance
+// costs one subtraction and one FMA per pair.  Entries whose boxes are at
+// least sqrt(42) alpha apart (list flag bit2) leave out the Gaussian of the
+// Coulomb SS, which is below 2^-60 there.
 //
 // FP64 kernel (plain form): one field per launch, float64 throughout,
 // absolute coordinates, libm exp and sqrt.
@@ -82,11 +88,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
-// Every kFold sources, each target's float32 partial sums are folded into its
+// Every kFold sources (record paths; every row of M proxies on the tensor
+// far path), each target's float32 partial sums are folded into its
 // two-float (hi, lo) accumulator by an error-free TwoSum.  Short folds keep
 // the float32 summation error small against the large subtracted term
 // c_i sum_j G w_j, which cancels against the analytic SS term.
-constexpr int kFold = 8;
+constexpr int kFold = 16;
 template <int NF, int TPT>
 __device__ __forceinline__ void fold(float (&acc)[TPT][NF], float (&hi)[TPT][NF], float (&lo)[TPT][NF])
 {
@@ -127,7 +134,9 @@ __device__ __forceinline__ void load_values(const float4* __restrict__ sv, int k
 
 // Far field: proxies, single-float positions relative to the batch center;
 //   Yukawa term  e^{-k r} / r * (qh - c w^),  Coulomb term (qh - c w^ e^{-r^2/a^2}) / r.
-template <int NY, bool HH, bool SS, int TPT>
+// GZ: the entry's Gaussian of the Coulomb SS is below float32 resolution for
+// every pair (list flag bit2), so the Hartree term is q / r alone.
+template <int NY, bool HH, bool SS, int TPT, bool GZ>
 __device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const float4* __restrict__ sv, int nk,
                                          const float (&tx)[TPT], const float (&ty)[TPT], const float (&tz)[TPT],
                                          const float (&nc)[TPT][NY + HH], float (&hi)[TPT][NY + HH],
@@ -160,7 +169,7 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const 
                 }
                 if (HH) {
                     float d;
-                    if (SS) {
+                    if (SS && !GZ) {
                         const float g = ex2_approx(kp.ga * r2);
                         d = fmaf(nc[j][NY] * s.w, g, qv[NY]);
                     } else {
@@ -174,13 +183,94 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const 
     }
 }
 
+// Far field on the tensor grid of one cluster's proxies (M nodes per
+// dimension): proxy (k1, k2, k3) sits at (X[k1], Y[k2], Z[k3]) relative to the
+// batch center, each coordinate rounded once to float32 exactly as the record
+// path rounds it, so r^2 = ((X - tx)^2 + (Y - ty)^2) + (Z - tz)^2 costs one
+// subtraction and one FMA per pair once the (k1, k2) part is formed; the
+// node coordinates are read from shared memory (broadcast).  The
+// tile holds whole k1-planes; sv holds per proxy q^ for the fields and w^ in
+// component NF.  Every row of M proxies is folded into the two-float sums.
+template <int NY, bool HH, bool SS, int TPT, int M, bool GZ>
+__device__ __forceinline__ void tile_far_tensor(const float* __restrict__ sX, const float* __restrict__ sY,
+                                                const float* __restrict__ sZ, const float4* __restrict__ sv, int np,
+                                                const float (&tx)[TPT], const float (&ty)[TPT],
+                                                const float (&tz)[TPT], const float (&nc)[TPT][NY + HH],
+                                                float (&hi)[TPT][NY + HH], float (&lo)[TPT][NY + HH],
+                                                const KParams& kp)
+{
+    constexpr int NF = NY + HH;
+    constexpr int GF = (NF + 4) / 4;  // float4 groups of (q^..., w^)
+    for (int pl = 0; pl < np; pl++) {
+        float dx2[TPT];
+#pragma unroll
+        for (int j = 0; j < TPT; j++) {
+            const float d = sX[pl] - tx[j];
+            dx2[j] = d * d;
+        }
+        for (int k2 = 0; k2 < M; k2++) {
+            float a[TPT];
+            const float yk = sY[k2];
+#pragma unroll
+            for (int j = 0; j < TPT; j++) {
+                const float d = yk - ty[j];
+                a[j] = fmaf(d, d, dx2[j]);
+            }
+            float acc[TPT][NF];
+#pragma unroll
+            for (int j = 0; j < TPT; j++)
+#pragma unroll
+                for (int o = 0; o < NF; o++) acc[j][o] = 0.0f;
+            const float4* row = sv + (pl * M + k2) * M;
+// partial unroll: measured fastest (full unroll leaves MUFU latency exposed)
+#pragma unroll 3
+            for (int k3 = 0; k3 < M; k3++) {
+                float qv[4 * GF];
+#pragma unroll
+                for (int g = 0; g < GF; g++) {
+                    const float4 t = row[g * kTile + k3];
+                    qv[4 * g] = t.x;
+                    qv[4 * g + 1] = t.y;
+                    qv[4 * g + 2] = t.z;
+                    qv[4 * g + 3] = t.w;
+                }
+                const float w = qv[NF];
+#pragma unroll
+                for (int j = 0; j < TPT; j++) {
+                    const float dz = sZ[k3] - tz[j];
+                    const float r2 = fmaf(dz, dz, a[j]);
+                    const float ri = rsqrt_approx(r2);
+                    const float r = r2 * ri;
+#pragma unroll
+                    for (int o = 0; o < NY; o++) {
+                        const float e = ex2_approx(kp.ky[o] * r);
+                        const float d = SS ? fmaf(nc[j][o], w, qv[o]) : qv[o];
+                        acc[j][o] = fmaf(e * ri, d, acc[j][o]);
+                    }
+                    if (HH) {
+                        float d;
+                        if (SS && !GZ) {
+                            const float g = ex2_approx(kp.ga * r2);
+                            d = fmaf(nc[j][NY] * w, g, qv[NY]);
+                        } else {
+                            d = qv[NY];
+                        }
+                        acc[j][NY] = fmaf(ri, d, acc[j][NY]);
+                    }
+                }
+            }
+            fold<NF, TPT>(acc, hi, lo);
+        }
+    }
+}
+
 // Near field: mesh points with positions relative to the batch center and
 // two-float field values f = fh + fl and weights w = wh + wl.  The SS
 // difference (fh_j - c_i) + fl_j, with c_i = fh_i, is exact up to one rounding
 // for close pairs (Sterbenz), where f_j - f_i cancels.
 //   Yukawa term  e^{-k r} / r * w_j (f_j - c_i),
 //   Coulomb term (rho_j - c_i e^{-r^2/a^2}) w_j / r.
-template <int NY, bool HH, bool SS, bool SELF, int TPT>
+template <int NY, bool HH, bool SS, bool SELF, int TPT, bool GZ>
 __device__ __forceinline__ void tile_near(const float4* __restrict__ srec, const float4* __restrict__ sv, int nk,
                                           const float (&tx)[TPT], const float (&ty)[TPT], const float (&tz)[TPT],
                                           const float (&nc)[TPT][NY + HH], float (&hi)[TPT][NY + HH],
@@ -216,7 +306,7 @@ __device__ __forceinline__ void tile_near(const float4* __restrict__ srec, const
                 }
                 if (HH) {
                     float d;
-                    if (SS) {
+                    if (SS && !GZ) {
                         const float g = ex2_approx(kp.ga * r2);
                         d = __fadd_rn(fmaf(nc[j][NY], g, v[NY]), v[NF + NY]);
                     } else {
@@ -230,7 +320,9 @@ __device__ __forceinline__ void tile_near(const float4* __restrict__ srec, const
     }
 }
 
-template <int NY, bool HH, bool SS>
+// M > 0: approximated clusters use the tensor-grid far path (degree M - 1);
+// M == 0: every entry goes through the record path.
+template <int NY, bool HH, bool SS, int M>
 __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item* __restrict__ items,
                                                            const Entry* __restrict__ ents,
                                                            const double* __restrict__ cen,
@@ -284,9 +376,54 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
         const double ox = cen[3 * f] - bx, oy = cen[3 * f + 1] - by, oz = cen[3 * f + 2] - bz;
         const bool far = en.flags & 2;
         const bool self = en.flags & 1;
+        const bool gz = en.flags & 4;
+        if constexpr (M > 0) {
+            if (far) {
+                // proxies k = (k1 M + k2) M + k3 of this cluster: records src0 + k
+                constexpr int PL = kTile / (M * M);  // k1-planes per tile
+                __shared__ float sX[M], sY[M], sZ[M];
+                __syncthreads();
+                if (tid < M) {
+                    const float4 rx = rec4[en.src0 + tid * M * M];
+                    const float4 ry = rec4[en.src0 + tid * M];
+                    const float4 rz = rec4[en.src0 + tid];
+                    sX[tid] = (float)((double)rx.x + ox);
+                    sY[tid] = (float)((double)ry.y + oy);
+                    sZ[tid] = (float)((double)rz.z + oz);
+                }
+                for (int p0 = 0; p0 < M; p0 += PL) {
+                    const int np = min(PL, M - p0);
+                    const int nk = np * M * M;
+                    const int base = en.src0 + p0 * M * M;
+                    __syncthreads();
+#pragma unroll
+                    for (int h = 0; h < kTile / THREADS; h++) {
+                        const int k = tid + h * THREADS;
+                        if (k < nk) {
+                            float v[4 * ((NF + 4) / 4)];
+#pragma unroll
+                            for (int m = 0; m < 4 * ((NF + 4) / 4); m++) v[m] = 0.0f;
+#pragma unroll
+                            for (int o = 0; o < NF; o++) v[o] = fa[o * lda + base + k];
+                            v[NF] = rec4[base + k].w;
+#pragma unroll
+                            for (int g = 0; g < (NF + 4) / 4; g++)
+                                sv[g * kTile + k] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                        }
+                    }
+                    __syncthreads();
+                    if (HH && SS && gz)
+                        tile_far_tensor<NY, HH, SS, TPT, M, HH && SS>(sX + p0, sY, sZ, sv, np, tx, ty, tz, nc, hi, lo,
+                                                                      kp);
+                    else
+                        tile_far_tensor<NY, HH, SS, TPT, M, false>(sX + p0, sY, sZ, sv, np, tx, ty, tz, nc, hi, lo, kp);
+                }
+                continue;
+            }
+        }
         for (int s0 = en.src0; s0 < en.src1; s0 += kTile) {
             const int ns = min(kTile, en.src1 - s0);
-            const int nk = (ns + 7) & ~7;
+            const int nk = (ns + 15) & ~15;
             __syncthreads();
 #pragma unroll
             for (int h = 0; h < kTile / THREADS; h++) {
@@ -324,12 +461,19 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
                         sv[g * kTile + k] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
             }
             __syncthreads();
-            if (far)
-                tile_far<NY, HH, SS, TPT>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
-            else if (self)
-                tile_near<NY, HH, SS, true, TPT>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
-            else
-                tile_near<NY, HH, SS, false, TPT>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+            constexpr bool G = HH && SS;  // a Gaussian to leave out exists
+            if (far) {
+                if (G && gz)
+                    tile_far<NY, HH, SS, TPT, G>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+                else
+                    tile_far<NY, HH, SS, TPT, false>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+            } else if (self) {
+                tile_near<NY, HH, SS, true, TPT, false>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+            } else if (G && gz) {
+                tile_near<NY, HH, SS, false, TPT, G>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+            } else {
+                tile_near<NY, HH, SS, false, TPT, false>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+            }
         }
     }
     double* out = part + ((size_t)blockIdx.x * nf_tot + field0) * kTargetsPerItem;
@@ -446,23 +590,30 @@ __global__ void __launch_bounds__(kThreads64) k_interact64(const Item* __restric
     part[((size_t)blockIdx.x * nf_tot + field) * kTargetsPerItem + tid] = acc;
 }
 
+template <int NY, bool HH, bool SS, int M>
+void launch32_m(Tree& T, const float* kyd, const float* q, const float* c, double* part, int nf_tot, int field0)
+{
+    launch(k_interact32<NY, HH, SS, M>, (int)T.nitems, Tpt<NY + HH>::threads, 0, T.stream, T.items.as<Item>(),
+           T.ent.as<Entry>(), T.cl_cen.as<double>(), T.rec4.as<float4>(), T.rec4lo.as<float4>(), q, T.nrec, c, T.n,
+           kyd, part, nf_tot, field0);
+}
+
 template <int NY, bool HH>
 void launch32_ss(Tree& T, bool ss, const float* kyd, const float* q, const float* c, double* part, int nf_tot,
                  int field0)
 {
-    // q: rows of fa (fh for points, qh for proxies), c: rows of fb (fl for points)
-    const int grid = (int)T.nitems;
-    cudaStream_t s = T.stream;
-    if (ss)
-        launch(k_interact32<NY, HH, true>, grid, Tpt<NY + HH>::threads, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
-                                                               T.cl_cen.as<double>(), T.rec4.as<float4>(),
-                                                               T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kyd, part,
-                                                               nf_tot, field0);
+    // q: rows of fa (fh for points, qh for proxies), c: rows of fb (fl for points).
+    // The tensor-grid far path serves degrees 6 and 8 with SS; others take
+    // the record path.
+    const int m = T.degree + 1;
+    if (ss && m == 9)
+        launch32_m<NY, HH, true, 9>(T, kyd, q, c, part, nf_tot, field0);
+    else if (ss && m == 7)
+        launch32_m<NY, HH, true, 7>(T, kyd, q, c, part, nf_tot, field0);
+    else if (ss)
+        launch32_m<NY, HH, true, 0>(T, kyd, q, c, part, nf_tot, field0);
     else
-        launch(k_interact32<NY, HH, false>, grid, Tpt<NY + HH>::threads, 0, s, T.items.as<Item>(), T.ent.as<Entry>(),
-                                                                T.cl_cen.as<double>(), T.rec4.as<float4>(),
-                                                                T.rec4lo.as<float4>(), q, T.nrec, c, T.n, kyd, part,
-                                                                nf_tot, field0);
+        launch32_m<NY, HH, false, 0>(T, kyd, q, c, part, nf_tot, field0);
     TAGI_LAUNCH_CHECK();
 }
 

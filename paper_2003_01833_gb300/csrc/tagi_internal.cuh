@@ -150,6 +150,7 @@ struct Tree {
     int nc = 0, nleaf = 0, depth = 0, nfar = 0;
     int64_t nent = 0, nitems = 0, ntchunk = 0, nant = 0, nrec = 0;
     int64_t near_pairs = 0, far_pairs = 0;
+    int64_t near_pairs_ng = 0, far_pairs_ng = 0;  // pairs of entries flagged bit2
 
     // points in tree order
     DevBuf perm;             // int[n] tree position -> caller index

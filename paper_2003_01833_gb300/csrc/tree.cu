@@ -463,6 +463,32 @@ __global__ void k_far_ranges(int64_t nent, Entry* ent, const int* cl_far, int64_
     }
 }
 
+// flags bit2: the boxes of the batch and of the source cluster are at least
+// sqrt(42) alpha apart, so exp(-r^2/alpha^2) <= 2^-60 for every pair of the
+// entry and the Gaussian of the Coulomb SS is below float32 resolution there
+// (the FP32C kernel leaves it out; the float64 kernel ignores the bit).
+// pairs[0], pairs[1]: near and far pairs of the flagged entries.
+__global__ void k_gauss_flags(int64_t nent, Entry* ent, const int* eb, const int* ec, const double* lo,
+                              const double* hi, const int* begin, const int* end, double alpha,
+                              unsigned long long* pairs)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nent) return;
+    const int b = eb[e], c = ec[e];
+    double d2 = 0.0;
+    for (int k = 0; k < 3; k++) {
+        const double g = fmax(0.0, fmax(lo[3 * c + k] - hi[3 * b + k], lo[3 * b + k] - hi[3 * c + k]));
+        d2 += g * g;
+    }
+    if (d2 >= 42.0 * alpha * alpha) {
+        Entry x = ent[e];
+        x.flags |= 4;
+        ent[e] = x;
+        const unsigned long long np = (unsigned long long)(end[b] - begin[b]) * (unsigned long long)(x.src1 - x.src0);
+        atomicAdd(pairs + ((x.flags & 2) ? 1 : 0), np);
+    }
+}
+
 // ---------------------------------------------------------------- work items
 __device__ __forceinline__ int padded(int v) { return (v + 7) & ~7; }
 
@@ -880,6 +906,18 @@ void build_tree(Tree& T, const double* xyz, const double* w)
     TAGI_REQUIRE(T.nrec < (int64_t)0x7fffffff, "too many source records");
     if (T.nent > 0)
         launch(k_far_ranges, nblocks(T.nent, 256), 256, 0, s, T.nent, T.ent.as<Entry>(), T.cl_far.as<int>(), n, T.P);
+    T.near_pairs_ng = T.far_pairs_ng = 0;
+    if (T.nent > 0) {
+        DevBuf ng;
+        ng.ensure(2 * sizeof(int64_t));
+        TAGI_CUDA(cudaMemsetAsync(ng.p, 0, 2 * sizeof(int64_t), s));
+        launch(k_gauss_flags, nblocks(T.nent, 256), 256, 0, s, T.nent, T.ent.as<Entry>(), T.ent_batch.as<int>(),
+               T.ent_clus.as<int>(), T.cl_lo.as<double>(), T.cl_hi.as<double>(), T.cl_begin.as<int>(),
+               T.cl_end.as<int>(), T.alpha, ng.as<unsigned long long>());
+        TAGI_LAUNCH_CHECK();
+        T.near_pairs_ng = read_i64(ng.as<int64_t>(), s, H);
+        T.far_pairs_ng = read_i64(ng.as<int64_t>() + 1, s, H);
+    }
     TAGI_LAUNCH_CHECK();
 
     // ---- work items of the near/far kernel
