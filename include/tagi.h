@@ -149,6 +149,16 @@ tagi_status tagi_yukawa_conv(tagi_tree* tree, const double* f, const double* k, 
  *   rho [dev] n float64; vh [dev] n float64, caller-owned. */
 tagi_status tagi_coulomb_conv(tagi_tree* tree, const double* rho, double* vh, void* stream);
 
+/* The convolutions of one Green iteration in a single pass over the
+ * geometry (one kernel launch per group of up to 8 fields): nf_y Yukawa
+ * fields with their own k, as tagi_yukawa_conv computes them, and, when rho
+ * is non-NULL, the Coulomb field of tagi_coulomb_conv.
+ *   f [dev] nf_y*n float64 (may be NULL if nf_y = 0); k [host] nf_y, each
+ *   finite and > 0; rho [dev] n or NULL; u [dev] nf_y*n and vh [dev] n,
+ *   caller-owned.  1 <= nf_y + (rho != NULL) <= 128. */
+tagi_status tagi_fields_conv(tagi_tree* tree, const double* f, const double* k, int nf_y, const double* rho,
+                             double* u, double* vh, void* stream);
+
 /* One Green iteration for nw orbitals at once (Algorithm 2 lines 3-6):
  *   f_o = (veff + vshift) psi_o, k_o = sqrt(-2 (eps_o + vshift))  (Eq. gauge-shift)
  *   psi~_o = -2 * Yukawa_{k_o}[f_o]                               (Eq. Yukawa)

@@ -401,6 +401,41 @@ tagi_status tagi_yukawa_conv(tagi_tree* tree, const double* f, const double* k, 
     });
 }
 
+tagi_status tagi_fields_conv(tagi_tree* tree, const double* f, const double* k, int nf_y, const double* rho,
+                             double* u, double* vh, void* stream)
+{
+    return guarded([&] {
+        Tree* T = as_tree(tree);
+        TAGI_REQUIRE(nf_y >= 0 && nf_y + (rho ? 1 : 0) >= 1, "no field to convolve");
+        TAGI_REQUIRE(nf_y + (rho ? 1 : 0) <= kMaxCallFields, "at most 128 fields per call");
+        TAGI_REQUIRE(nf_y == 0 || (f != nullptr && k != nullptr && u != nullptr), "f, k or u is NULL");
+        TAGI_REQUIRE(rho == nullptr || vh != nullptr, "vh is required when rho is given");
+        for (int o = 0; o < nf_y; o++) TAGI_REQUIRE(std::isfinite(k[o]) && k[o] > 0.0, "every k must be finite and > 0");
+        T->stream = (cudaStream_t)stream;
+        AllocStream as(T->stream);
+        const int nf = nf_y + (rho ? 1 : 0);
+        const size_t n = (size_t)T->n;
+        T->fbuf.ensure(sizeof(double) * nf * n);
+        double* fb = T->fbuf.as<double>();
+        if (nf_y)
+            TAGI_CUDA(cudaMemcpyAsync(fb, f, sizeof(double) * nf_y * n, cudaMemcpyDeviceToDevice, T->stream));
+        if (rho) TAGI_CUDA(cudaMemcpyAsync(fb + nf_y * n, rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, T->stream));
+        RateSrc R = host_rates(*T, nf);
+        std::vector<double*> out(nf);
+        for (int o = 0; o < nf_y; o++) {
+            R.val[o] = k[o];
+            out[o] = u + o * n;
+        }
+        if (rho) {
+            R.kind[nf_y] = 1;
+            R.val[nf_y] = T->alpha;
+            out[nf_y] = vh;
+        }
+        clear_err(*T);
+        run_convolution(*T, fb, R, nullptr, out.data());
+    });
+}
+
 tagi_status tagi_coulomb_conv(tagi_tree* tree, const double* rho, double* vh, void* stream)
 {
     return guarded([&] {

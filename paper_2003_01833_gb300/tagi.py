@@ -97,6 +97,7 @@ def lib():
         L.tagi_anterpolate.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp]
         L.tagi_yukawa_conv.argtypes = [_vp, _vp, _D, ctypes.c_int, _vp, _vp]
         L.tagi_coulomb_conv.argtypes = [_vp, _vp, _vp, _vp]
+        L.tagi_fields_conv.argtypes = [_vp, _vp, _D, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.tagi_green_step.argtypes = [_vp, _vp, ctypes.c_double, _vp, _D, ctypes.c_int, _vp, _vp, _D, _D, _vp]
         L.tagi_kernel_launches.restype = ctypes.c_int64
         L.tagi_green_iterate.argtypes = [_vp, _vp, ctypes.c_double, _vp, _D, ctypes.c_int,
@@ -256,6 +257,22 @@ def tagi_coulomb_conv(tree, rho, vh, stream=None):
     if rho.numel() != _tree_n(tree):
         raise ValueError("rho must have n elements")
     _check(lib().tagi_coulomb_conv(tree, _dptr(rho, "rho"), _dptr(vh, "vh", rho.numel()), _stream(stream)))
+
+
+def tagi_fields_conv(tree, f, k, u, rho=None, vh=None, stream=None):
+    """Yukawa fields f (nf_y, n) with decay rates k into u, and the Coulomb
+    field of rho into vh, in one pass (float64 CUDA tensors; f and u may be
+    None when only rho is given)."""
+    n = _tree_n(tree)
+    nf_y = 0 if f is None else (f.shape[0] if f.dim() == 2 else 1)
+    if (f is not None and (f.numel() != nf_y * n or u is None or u.numel() != nf_y * n)) or (
+            rho is not None and (rho.numel() != n or vh is None or vh.numel() != n)):
+        raise ValueError("f and u must be (nf_y, n); rho and vh must have n elements")
+    ka = np.ascontiguousarray(np.atleast_1d(k if k is not None else []), dtype=np.float64)
+    if ka.size != nf_y:
+        raise ValueError("one decay rate per Yukawa field")
+    _check(lib().tagi_fields_conv(tree, _dptr(f, "f"), ka.ctypes.data_as(_D), nf_y, _dptr(rho, "rho"),
+                                  _dptr(u, "u"), _dptr(vh, "vh"), _stream(stream)))
 
 
 def tagi_green_step(tree, veff, vshift, psi, eps, rho=None, vh=None, stream=None):

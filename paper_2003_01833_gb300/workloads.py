@@ -503,7 +503,7 @@ def lithium(seed: int = 1, tol_m: float = 3e-7, p: int = 4, half_width: float = 
                     meta={"seed": seed, "tol_m": tol_m}, vext=vx, n_elec=3.0, e_zz=0.0)
 
 
-def carbon_monoxide(seed: int = 2, tol_m: float = 3e-6, p: int = 4, half_width: float = 20.0,
+def carbon_monoxide(seed: int = 2, tol_m: float = 1e-8, p: int = 4, half_width: float = 20.0,
                     n_orb: int = 7, uniform_levels: int = 3) -> Workload:
     """CO with C at (-1.06581,0,0) and O at (+1.06581,0,0) (Section 6):
     adaptive mesh, n_orb orbitals from a seeded superposition of atomic
@@ -513,7 +513,7 @@ def carbon_monoxide(seed: int = 2, tol_m: float = 3e-6, p: int = 4, half_width: 
     return _molecule_workload("CO", mol, mesh, seed, n_orb)
 
 
-def benzene(seed: int = 3, tol_m: float = 3e-6, p: int = 4, half_width: float = 20.0,
+def benzene(seed: int = 3, tol_m: float = 3e-8, p: int = 4, half_width: float = 20.0,
             n_orb: int = 21, uniform_levels: int = 3) -> Workload:
     """C6H6 in the z=0 plane at the paper's geometry (Section 6)."""
     C = [(-0.682781, 2.548170), (0.682781, -2.548170), (2.548230, -0.682767), (-2.548230, 0.682767),
