@@ -357,97 +357,147 @@ struct ListArgs {
     int P;
 };
 
-// Algorithm 3's ComputePotential for one batch, as an explicit DFS.  In
-// count mode (out == nullptr) it returns entry counts; in fill mode it writes.
-template <bool FILL>
-__device__ void walk(const ListArgs a, int batch, int limit, int* nent, int64_t* near_src, int64_t* far_src,
-                     Entry* out, int* out_batch, int* out_clus, int* is_far, int* err)
+// Algorithm 3's ComputePotential for one batch, one warp per batch: the
+// clusters to visit form a frontier (level by level from the root), each lane
+// applies the MAC to one cluster, and warp prefix sums place the entries and
+// the opened children in lane order, so the output order is deterministic.
+// In count mode (FILL false) only counts are produced.  The MAC arithmetic is
+// the float64 expression of the oracle, without contraction.
+constexpr int kListWarps = 2;      // warps (batches) per CTA
+constexpr int kFront = 1024;       // frontier capacity per warp and level
+
+__device__ __forceinline__ int warp_excl(int v, int lane, int* total)
 {
-    int stack[512];
-    int top = 0;
-    stack[top++] = 0;
-    int cnt = 0;
-    int64_t ns_near = 0, ns_far = 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+template <bool FILL>
+__device__ void walk_warp(const ListArgs a, int batch, int limit, int* front, int* nent, int64_t* near_src,
+                          int64_t* far_src, Entry* out, int* out_batch, int* out_clus, int* is_far, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    int* cur = front;
+    int* nxt = front + kFront;
+    if (lane == 0) cur[0] = 0;
+    __syncwarp();
+    int ncur = 1, cnt = 0;
+    int64_t sn = 0, sf = 0;  // per lane
     const double bx = a.cen[3 * batch], by = a.cen[3 * batch + 1], bz = a.cen[3 * batch + 2];
     const double rb = a.rad[batch];
-    while (top > 0) {
-        int c = stack[--top];
-        double dx = __dsub_rn(bx, a.cen[3 * c]), dy = __dsub_rn(by, a.cen[3 * c + 1]),
-               dz = __dsub_rn(bz, a.cen[3 * c + 2]);
-        double R = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-        bool theta_ok = __ddiv_rn(__dadd_rn(rb, a.rad[c]), R) < a.theta;
-        int ns = a.end[c] - a.begin[c];
-        bool size_ok = a.P < ns;
-        if (theta_ok && size_ok) {
-            if (FILL && cnt >= limit) {
-                *err = 1;
-                return;
-            }
-            if (FILL) {
-                out[cnt] = Entry{0, 0, c, 2};
-                out_batch[cnt] = batch;
-                out_clus[cnt] = c;
-                is_far[c] = 1;
-            }
-            cnt++;
-            ns_far += a.P;
-        } else if (!theta_ok && a.nch[c] > 0) {
-            int k = a.nch[c];
-            if (top + k > 512) {
-                *err = 1;
-                return;
-            }
-            for (int q = k - 1; q >= 0; q--) stack[top++] = a.child[8 * c + q];
-        } else {
-            // direct sum with every point of c: one entry per leaf below it
-            int p = a.begin[c];
-            while (p < a.end[c]) {
-                int leaf = a.pt_leaf[p];
-                int e = a.end[leaf];
-                if (FILL && cnt >= limit) {
-                    *err = 1;
-                    return;
+    while (ncur > 0) {
+        int nnext = 0;
+        for (int base = 0; base < ncur; base += 32) {
+            const int i = base + lane;
+            int c = -1, kind = 0, ne = 0, nch = 0;  // kind: 1 far, 2 open, 3 direct
+            if (i < ncur) {
+                c = cur[i];
+                const double dx = __dsub_rn(bx, a.cen[3 * c]), dy = __dsub_rn(by, a.cen[3 * c + 1]),
+                             dz = __dsub_rn(bz, a.cen[3 * c + 2]);
+                const double R =
+                    __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+                const bool theta_ok = __ddiv_rn(__dadd_rn(rb, a.rad[c]), R) < a.theta;
+                const bool size_ok = a.P < a.end[c] - a.begin[c];
+                if (theta_ok && size_ok) {
+                    kind = 1;
+                    ne = 1;
+                } else if (!theta_ok && a.nch[c] > 0) {
+                    kind = 2;
+                    nch = a.nch[c];
+                } else {
+                    // direct sum with every point of c: one entry per leaf below it
+                    kind = 3;
+                    for (int p = a.begin[c]; p < a.end[c]; p = a.end[a.pt_leaf[p]]) ne++;
                 }
+            }
+            int etot, ctot;
+            const int eoff = warp_excl(ne, lane, &etot);
+            const int coff = warp_excl(nch, lane, &ctot);
+            if ((FILL && cnt + etot > limit) || nnext + ctot > kFront) {
+                if (lane == 0) *err = 1;
+                return;
+            }
+            if (kind == 2)
+                for (int q = 0; q < nch; q++) nxt[nnext + coff + q] = a.child[8 * c + q];
+            if (kind == 1) {
+                sf += a.P;
                 if (FILL) {
-                    out[cnt] = Entry{a.begin[leaf], e, leaf, leaf == batch ? 1 : 0};
-                    out_batch[cnt] = batch;
-                    out_clus[cnt] = leaf;
+                    out[cnt + eoff] = Entry{0, 0, c, 2};
+                    out_batch[cnt + eoff] = batch;
+                    out_clus[cnt + eoff] = c;
+                    is_far[c] = 1;
                 }
-                cnt++;
-                ns_near += e - a.begin[leaf];
-                p = e;
+            } else if (kind == 3) {
+                int t = 0;
+                for (int p = a.begin[c]; p < a.end[c];) {
+                    const int leaf = a.pt_leaf[p];
+                    const int e = a.end[leaf];
+                    if (FILL) {
+                        out[cnt + eoff + t] = Entry{a.begin[leaf], e, leaf, leaf == batch ? 1 : 0};
+                        out_batch[cnt + eoff + t] = batch;
+                        out_clus[cnt + eoff + t] = leaf;
+                    }
+                    sn += e - a.begin[leaf];
+                    t++;
+                    p = e;
+                }
             }
+            cnt += etot;
+            nnext += ctot;
         }
+        __syncwarp();
+        int* t = cur;
+        cur = nxt;
+        nxt = t;
+        ncur = nnext;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sn += __shfl_down_sync(0xffffffffu, sn, o);
+        sf += __shfl_down_sync(0xffffffffu, sf, o);
     }
     *nent = cnt;
-    *near_src = ns_near;
-    *far_src = ns_far;
+    *near_src = sn;  // lane 0 holds the sums
+    *far_src = sf;
 }
 
-__global__ void k_list_count(ListArgs a, int nleaf, int64_t* cnt, int64_t* near_pairs, int64_t* far_pairs, int* err)
+__global__ void __launch_bounds__(32 * kListWarps) k_list_count(ListArgs a, int nleaf, int64_t* cnt,
+                                                                 int64_t* near_pairs, int64_t* far_pairs, int* err)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int front[kListWarps][2 * kFront];
+    const int w = threadIdx.x >> 5;
+    const int j = blockIdx.x * kListWarps + w;
     if (j >= nleaf) return;
-    int b = a.leaves[j];
-    int ne;
-    int64_t sn, sf;
-    walk<false>(a, b, 0, &ne, &sn, &sf, nullptr, nullptr, nullptr, nullptr, err);
-    cnt[j] = ne;
-    int64_t nb = a.end[b] - a.begin[b];
-    near_pairs[j] = nb * sn;
-    far_pairs[j] = nb * sf;
+    const int b = a.leaves[j];
+    int ne = 0;
+    int64_t sn = 0, sf = 0;
+    walk_warp<false>(a, b, 0, front[w], &ne, &sn, &sf, nullptr, nullptr, nullptr, nullptr, err);
+    if ((threadIdx.x & 31) == 0) {
+        cnt[j] = ne;
+        const int64_t nb = a.end[b] - a.begin[b];
+        near_pairs[j] = nb * sn;
+        far_pairs[j] = nb * sf;
+    }
 }
 
-__global__ void k_list_fill(ListArgs a, int nleaf, const int64_t* off, Entry* ent, int* eb, int* ec, int* is_far,
-                            int* err)
+__global__ void __launch_bounds__(32 * kListWarps) k_list_fill(ListArgs a, int nleaf, const int64_t* off, Entry* ent,
+                                                                int* eb, int* ec, int* is_far, int* err)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int front[kListWarps][2 * kFront];
+    const int w = threadIdx.x >> 5;
+    const int j = blockIdx.x * kListWarps + w;
     if (j >= nleaf) return;
-    int b = a.leaves[j];
+    const int b = a.leaves[j];
     int ne;
     int64_t sn, sf;
-    int64_t o = off[j];
-    walk<true>(a, b, (int)(off[j + 1] - o), &ne, &sn, &sf, ent + o, eb + o, ec + o, is_far, err);
+    const int64_t o = off[j];
+    walk_warp<true>(a, b, (int)(off[j + 1] - o), front[w], &ne, &sn, &sf, ent + o, eb + o, ec + o, is_far, err);
 }
 
 __global__ void k_far_ranges(int64_t nent, Entry* ent, const int* cl_far, int64_t n, int P)
@@ -854,7 +904,7 @@ void build_tree(Tree& T, const double* xyz, const double* w)
     fpair.ensure(8 * ((size_t)nleaf + 1));
     err.ensure(16);
     TAGI_CUDA(cudaMemsetAsync(err.p, 0, 16, s));
-    launch(k_list_count, nblocks(nleaf, 64), 64, 0, s, la, nleaf, lc.as<int64_t>(), npair.as<int64_t>(),
+    launch(k_list_count, nblocks(nleaf, kListWarps), 32 * kListWarps, 0, s, la, nleaf, lc.as<int64_t>(), npair.as<int64_t>(),
                                                    fpair.as<int64_t>(), err.as<int>());
     exclusive_scan_i64(lc.as<int64_t>(), lo_.as<int64_t>(), nleaf, s);
     TAGI_LAUNCH_CHECK();
@@ -877,7 +927,7 @@ void build_tree(Tree& T, const double* xyz, const double* w)
     DevBuf isfar;
     isfar.ensure(4 * (size_t)nc);
     TAGI_CUDA(cudaMemsetAsync(isfar.p, 0, 4 * (size_t)nc, s));
-    launch(k_list_fill, nblocks(nleaf, 64), 64, 0, s, la, nleaf, lo_.as<int64_t>(), T.ent.as<Entry>(),
+    launch(k_list_fill, nblocks(nleaf, kListWarps), 32 * kListWarps, 0, s, la, nleaf, lo_.as<int64_t>(), T.ent.as<Entry>(),
                                                   T.ent_batch.as<int>(), T.ent_clus.as<int>(), isfar.as<int>(),
                                                   err.as<int>());
     TAGI_LAUNCH_CHECK();
