@@ -13,7 +13,9 @@
 // 1/(4 pi) of G_k are added by the epilogue.
 //
 // FP32C kernel: all fields of a call (each Yukawa field with its own k, plus
-// the Hartree field) share one pass over the geometry.  Each CTA owns up to
+// the Hartree field) share one pass over the geometry.  Targets are held in
+// pairs, and the near field runs on two targets per instruction with the
+// packed f32x2 FMA/add/multiply (same rounding per lane as scalar code).  Each CTA owns up to
 // 256 targets of one batch (64 threads x 4 targets, or 128 x 2 for launches
 // with more than 4 fields) and a contiguous segment
 // of the batch's interaction list; source tiles of 256 records are staged in
@@ -132,15 +134,25 @@ __device__ __forceinline__ void load_values(const float4* __restrict__ sv, int k
     }
 }
 
+// Targets live in pairs: target 2i is lane x and target 2i+1 lane y of pair i,
+// with the coordinates stored negated (s - t is computed as s + (-t), the same
+// IEEE result).  Scalar code reads one lane; j is a compile-time index once
+// the target loops are unrolled.
+__device__ __forceinline__ float lane(const float2& v, int j) { return (j & 1) ? v.y : v.x; }
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // Far field: proxies, single-float positions relative to the batch center;
 //   Yukawa term  e^{-k r} / r * (qh - c w^),  Coulomb term (qh - c w^ e^{-r^2/a^2}) / r.
 // GZ: the entry's Gaussian of the Coulomb SS is below float32 resolution for
 // every pair (list flag bit2), so the Hartree term is q / r alone.
 template <int NY, bool HH, bool SS, int TPT, bool GZ>
 __device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const float4* __restrict__ sv, int nk,
-                                         const float (&tx)[TPT], const float (&ty)[TPT], const float (&tz)[TPT],
-                                         const float (&nc)[TPT][NY + HH], float (&hi)[TPT][NY + HH],
-                                         float (&lo)[TPT][NY + HH], const KParams& kp)
+                                         const float2 (&ntx)[TPT / 2], const float2 (&nty)[TPT / 2],
+                                         const float2 (&ntz)[TPT / 2], const float2 (&nc)[TPT / 2][NY + HH],
+                                         float (&hi)[TPT][NY + HH], float (&lo)[TPT][NY + HH], const KParams& kp)
 {
     constexpr int NF = NY + HH;
     constexpr int G = TileLayout<NF>::G;
@@ -157,21 +169,22 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const 
             load_values<NF>(sv, k, qv);
 #pragma unroll
             for (int j = 0; j < TPT; j++) {
-                const float dx = s.x - tx[j], dy = s.y - ty[j], dz = s.z - tz[j];
+                const float dx = s.x + lane(ntx[j >> 1], j), dy = s.y + lane(nty[j >> 1], j),
+                            dz = s.z + lane(ntz[j >> 1], j);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 const float ri = rsqrt_approx(r2);
                 const float r = r2 * ri;
 #pragma unroll
                 for (int o = 0; o < NY; o++) {
                     const float e = ex2_approx(kp.ky[o] * r);
-                    const float d = SS ? fmaf(nc[j][o], s.w, qv[o]) : qv[o];
+                    const float d = SS ? fmaf(lane(nc[j >> 1][o], j), s.w, qv[o]) : qv[o];
                     acc[j][o] = fmaf(e * ri, d, acc[j][o]);
                 }
                 if (HH) {
                     float d;
                     if (SS && !GZ) {
                         const float g = ex2_approx(kp.ga * r2);
-                        d = fmaf(nc[j][NY] * s.w, g, qv[NY]);
+                        d = fmaf(lane(nc[j >> 1][NY], j) * s.w, g, qv[NY]);
                     } else {
                         d = qv[NY];
                     }
@@ -188,14 +201,14 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const 
 // batch center, each coordinate rounded once to float32 exactly as the record
 // path rounds it, so r^2 = ((X - tx)^2 + (Y - ty)^2) + (Z - tz)^2 costs one
 // subtraction and one FMA per pair once the (k1, k2) part is formed; the
-// node coordinates are read from shared memory (broadcast).  The
-// tile holds whole k1-planes; sv holds per proxy q^ for the fields and w^ in
-// component NF.  Every row of M proxies is folded into the two-float sums.
+// node coordinates are read from shared memory (broadcast).  The tile holds
+// whole k1-planes; sv holds per proxy q^ for the fields and w^ in component
+// NF.  Every row of M proxies is folded into the two-float sums.
 template <int NY, bool HH, bool SS, int TPT, int M, bool GZ>
 __device__ __forceinline__ void tile_far_tensor(const float* __restrict__ sX, const float* __restrict__ sY,
                                                 const float* __restrict__ sZ, const float4* __restrict__ sv, int np,
-                                                const float (&tx)[TPT], const float (&ty)[TPT],
-                                                const float (&tz)[TPT], const float (&nc)[TPT][NY + HH],
+                                                const float2 (&ntx)[TPT / 2], const float2 (&nty)[TPT / 2],
+                                                const float2 (&ntz)[TPT / 2], const float2 (&nc)[TPT / 2][NY + HH],
                                                 float (&hi)[TPT][NY + HH], float (&lo)[TPT][NY + HH],
                                                 const KParams& kp)
 {
@@ -205,7 +218,7 @@ __device__ __forceinline__ void tile_far_tensor(const float* __restrict__ sX, co
         float dx2[TPT];
 #pragma unroll
         for (int j = 0; j < TPT; j++) {
-            const float d = sX[pl] - tx[j];
+            const float d = sX[pl] + lane(ntx[j >> 1], j);
             dx2[j] = d * d;
         }
         for (int k2 = 0; k2 < M; k2++) {
@@ -213,7 +226,7 @@ __device__ __forceinline__ void tile_far_tensor(const float* __restrict__ sX, co
             const float yk = sY[k2];
 #pragma unroll
             for (int j = 0; j < TPT; j++) {
-                const float d = yk - ty[j];
+                const float d = yk + lane(nty[j >> 1], j);
                 a[j] = fmaf(d, d, dx2[j]);
             }
             float acc[TPT][NF];
@@ -222,7 +235,7 @@ __device__ __forceinline__ void tile_far_tensor(const float* __restrict__ sX, co
 #pragma unroll
                 for (int o = 0; o < NF; o++) acc[j][o] = 0.0f;
             const float4* row = sv + (pl * M + k2) * M;
-// partial unroll: measured fastest (full unroll leaves MUFU latency exposed)
+            // partial unroll: measured fastest (full unroll leaves MUFU latency exposed)
 #pragma unroll 3
             for (int k3 = 0; k3 < M; k3++) {
                 float qv[4 * GF];
@@ -237,21 +250,21 @@ __device__ __forceinline__ void tile_far_tensor(const float* __restrict__ sX, co
                 const float w = qv[NF];
 #pragma unroll
                 for (int j = 0; j < TPT; j++) {
-                    const float dz = sZ[k3] - tz[j];
+                    const float dz = sZ[k3] + lane(ntz[j >> 1], j);
                     const float r2 = fmaf(dz, dz, a[j]);
                     const float ri = rsqrt_approx(r2);
                     const float r = r2 * ri;
 #pragma unroll
                     for (int o = 0; o < NY; o++) {
                         const float e = ex2_approx(kp.ky[o] * r);
-                        const float d = SS ? fmaf(nc[j][o], w, qv[o]) : qv[o];
+                        const float d = SS ? fmaf(lane(nc[j >> 1][o], j), w, qv[o]) : qv[o];
                         acc[j][o] = fmaf(e * ri, d, acc[j][o]);
                     }
                     if (HH) {
                         float d;
                         if (SS && !GZ) {
                             const float g = ex2_approx(kp.ga * r2);
-                            d = fmaf(nc[j][NY] * w, g, qv[NY]);
+                            d = fmaf(lane(nc[j >> 1][NY], j) * w, g, qv[NY]);
                         } else {
                             d = qv[NY];
                         }
@@ -264,59 +277,101 @@ __device__ __forceinline__ void tile_far_tensor(const float* __restrict__ sX, co
     }
 }
 
+// Shared layout of a staged near-field tile: per source the float2 values
+// x, y, z, w_hi, w_lo, fh[NF], fl[NF], each duplicated into both lanes, packed
+// two to a float4.
+template <int NF>
+struct NearLayout {
+    static constexpr int NV2 = 5 + 2 * NF;
+    static constexpr int NV4 = (NV2 + 1) / 2;
+};
+
+// The fields' exponent factors duplicated into both lanes.
+struct KParams2 {
+    float2 ky[8];
+    float2 ga;
+};
+
+// Fold of pair accumulators: lane x of pair i belongs to target 2i, lane y
+// to target 2i+1; the same TwoSum as fold().
+template <int NF, int TPT>
+__device__ __forceinline__ void fold2(float2 (&acc)[TPT / 2][NF], float (&hi)[TPT][NF], float (&lo)[TPT][NF])
+{
+#pragma unroll
+    for (int j = 0; j < TPT; j++)
+#pragma unroll
+        for (int o = 0; o < NF; o++) {
+            float sum, er;
+            two_sum(hi[j][o], lane(acc[j >> 1][o], j), sum, er);
+            hi[j][o] = sum;
+            lo[j][o] += er;
+        }
+}
+
 // Near field: mesh points with positions relative to the batch center and
 // two-float field values f = fh + fl and weights w = wh + wl.  The SS
 // difference (fh_j - c_i) + fl_j, with c_i = fh_i, is exact up to one rounding
 // for close pairs (Sterbenz), where f_j - f_i cancels.
 //   Yukawa term  e^{-k r} / r * w_j (f_j - c_i),
 //   Coulomb term (rho_j - c_i e^{-r^2/a^2}) w_j / r.
+// Two targets per instruction (f32x2), each lane rounding exactly as the
+// scalar form would.
 template <int NY, bool HH, bool SS, bool SELF, int TPT, bool GZ>
-__device__ __forceinline__ void tile_near(const float4* __restrict__ srec, const float4* __restrict__ sv, int nk,
-                                          const float (&tx)[TPT], const float (&ty)[TPT], const float (&tz)[TPT],
-                                          const float (&nc)[TPT][NY + HH], float (&hi)[TPT][NY + HH],
-                                          float (&lo)[TPT][NY + HH], const KParams& kp)
+__device__ __forceinline__ void tile_near(const float4* __restrict__ sn, int nk, const float2 (&ntx)[TPT / 2],
+                                          const float2 (&nty)[TPT / 2], const float2 (&ntz)[TPT / 2],
+                                          const float2 (&nc)[TPT / 2][NY + HH], float (&hi)[TPT][NY + HH],
+                                          float (&lo)[TPT][NY + HH], const KParams2& kp)
 {
     constexpr int NF = NY + HH;
-    constexpr int G = TileLayout<NF>::G;
+    constexpr int NP = TPT / 2;
+    constexpr int NV4 = NearLayout<NF>::NV4;
     for (int k0 = 0; k0 < nk; k0 += kFold) {
-        float acc[TPT][NF];
+        float2 acc[NP][NF];
 #pragma unroll
-        for (int j = 0; j < TPT; j++)
+        for (int j = 0; j < NP; j++)
 #pragma unroll
-            for (int o = 0; o < NF; o++) acc[j][o] = 0.0f;
+            for (int o = 0; o < NF; o++) acc[j][o] = make_float2(0.0f, 0.0f);
 #pragma unroll 2
         for (int k = k0; k < k0 + kFold; k++) {
-            const float4 s = srec[k];
-            float v[4 * G];
-            load_values<NF>(sv, k, v);
+            float2 v[2 * NV4];  // 0 x, 1 y, 2 z, 3 w_hi, 4 w_lo, 5 + o fh, 5 + NF + o fl
 #pragma unroll
-            for (int j = 0; j < TPT; j++) {
-                const float dx = s.x - tx[j], dy = s.y - ty[j], dz = s.z - tz[j];
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                float ri = rsqrt_approx(r2);
-                if (SELF) ri = r2 > 0.0f ? ri : 0.0f;
-                const float r = r2 * ri;
-                const float riw = fmaf(ri, v[2 * NF], ri * s.w);  // ri (w_hi + w_lo)
+            for (int g = 0; g < NV4; g++) {
+                const float4 t = sn[g * kTile + k];
+                v[2 * g] = make_float2(t.x, t.y);
+                v[2 * g + 1] = make_float2(t.z, t.w);
+            }
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                const float2 dx = add2(v[0], ntx[j]), dy = add2(v[1], nty[j]), dz = add2(v[2], ntz[j]);
+                const float2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                if (SELF) {
+                    ri.x = r2.x > 0.0f ? ri.x : 0.0f;
+                    ri.y = r2.y > 0.0f ? ri.y : 0.0f;
+                }
+                const float2 r = mul2(r2, ri);
+                const float2 riw = fma2(ri, v[4], mul2(ri, v[3]));  // ri (w_hi + w_lo)
 #pragma unroll
                 for (int o = 0; o < NY; o++) {
-                    const float e = ex2_approx(kp.ky[o] * r);
-                    const float d =
-                        SS ? __fadd_rn(__fadd_rn(v[o], nc[j][o]), v[NF + o]) : __fadd_rn(v[o], v[NF + o]);
-                    acc[j][o] = fmaf(e * riw, d, acc[j][o]);
+                    const float2 t = mul2(kp.ky[o], r);
+                    const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+                    const float2 d = SS ? add2(add2(v[5 + o], nc[j][o]), v[5 + NF + o]) : add2(v[5 + o], v[5 + NF + o]);
+                    acc[j][o] = fma2(mul2(e, riw), d, acc[j][o]);
                 }
                 if (HH) {
-                    float d;
+                    float2 d;
                     if (SS && !GZ) {
-                        const float g = ex2_approx(kp.ga * r2);
-                        d = __fadd_rn(fmaf(nc[j][NY], g, v[NY]), v[NF + NY]);
+                        const float2 t = mul2(kp.ga, r2);
+                        const float2 g = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+                        d = add2(fma2(nc[j][NY], g, v[5 + NY]), v[5 + NF + NY]);
                     } else {
-                        d = __fadd_rn(v[NY], v[NF + NY]);
+                        d = add2(v[5 + NY], v[5 + NF + NY]);
                     }
-                    acc[j][NY] = fmaf(riw, d, acc[j][NY]);
+                    acc[j][NY] = fma2(riw, d, acc[j][NY]);
                 }
             }
         }
-        fold<NF, TPT>(acc, hi, lo);
+        fold2<NF, TPT>(acc, hi, lo);
     }
 }
 
@@ -335,21 +390,36 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
 {
     constexpr int NF = NY + HH;
     constexpr int G = TileLayout<NF>::G;
+    constexpr int GF = (NF + 4) / 4;
+    constexpr int NV4 = NearLayout<NF>::NV4;
     constexpr int TPT = Tpt<NF>::value;
+    constexpr int NP = TPT / 2;
     constexpr int THREADS = Tpt<NF>::threads;
+    constexpr int SB = NV4 > 1 + G ? NV4 : 1 + G;  // float4 per staged source, largest layout
+    static_assert(GF <= SB, "tensor layout fits");
     // exponent factors of this launch's fields, from device memory so that a
     // captured graph picks up the current eigenvalues on every replay
     KParams kp{};
+    KParams2 kp2{};
 #pragma unroll
-    for (int o = 0; o < NY; o++) kp.ky[o] = kyd[o];
-    if (HH) kp.ga = kyd[NY];
-    __shared__ float4 srec[kTile];
-    __shared__ float4 sv[G * kTile];
+    for (int o = 0; o < NY; o++) {
+        kp.ky[o] = kyd[o];
+        kp2.ky[o] = make_float2(kp.ky[o], kp.ky[o]);
+    }
+    if (HH) {
+        kp.ga = kyd[NY];
+        kp2.ga = make_float2(kp.ga, kp.ga);
+    }
+    __shared__ float4 sbuf[SB * kTile];
+    float4* const srec = sbuf;         // record path: positions and w
+    float4* const sv = sbuf + kTile;   // record path: values
+    float4* const sn = sbuf;           // near field: duplicated float2 values
+    float4* const st = sbuf;           // tensor far path: (q^, w^)
 
     const Item it = items[blockIdx.x];
     const int tid = threadIdx.x;
-    float tx[TPT], ty[TPT], tz[TPT];
-    float nc[TPT][NF];
+    float2 ntx[NP], nty[NP], ntz[NP];
+    float2 nc[NP][NF];
     float hi[TPT][NF], lo[TPT][NF];
 #pragma unroll
     for (int j = 0; j < TPT; j++) {
@@ -359,16 +429,30 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
         const float4 rl = ok ? rec4lo[p] : make_float4(0.f, 0.f, 0.f, 0.f);
         // rounded exactly as a staged source of the batch's own leaf, so the
         // self pair gives r = 0 bit for bit
-        tx[j] = (float)(((double)r.x + (double)rl.x) + 0.0);
-        ty[j] = (float)(((double)r.y + (double)rl.y) + 0.0);
-        tz[j] = (float)(((double)r.z + (double)rl.z) + 0.0);
+        const float x = -(float)(((double)r.x + (double)rl.x) + 0.0);
+        const float y = -(float)(((double)r.y + (double)rl.y) + 0.0);
+        const float z = -(float)(((double)r.z + (double)rl.z) + 0.0);
+        if (j & 1) {
+            ntx[j >> 1].y = x;
+            nty[j >> 1].y = y;
+            ntz[j >> 1].y = z;
+        } else {
+            ntx[j >> 1].x = x;
+            nty[j >> 1].x = y;
+            ntz[j >> 1].x = z;
+        }
 #pragma unroll
         for (int o = 0; o < NF; o++) {
-            nc[j][o] = ok ? -fa[o * lda + p] : 0.0f;  // SS constant c_i = fh_i
+            const float c = ok ? -fa[o * lda + p] : 0.0f;  // SS constant c_i = fh_i
+            if (j & 1)
+                nc[j >> 1][o].y = c;
+            else
+                nc[j >> 1][o].x = c;
             hi[j][o] = lo[j][o] = 0.0f;
         }
     }
     const double bx = cen[3 * it.batch], by = cen[3 * it.batch + 1], bz = cen[3 * it.batch + 2];
+    constexpr bool GZOK = HH && SS;  // a Gaussian to leave out exists
 
     for (int e = it.e0; e < it.e1; e++) {
         const Entry en = ents[e];
@@ -400,23 +484,24 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
                     for (int h = 0; h < kTile / THREADS; h++) {
                         const int k = tid + h * THREADS;
                         if (k < nk) {
-                            float v[4 * ((NF + 4) / 4)];
+                            float v[4 * GF];
 #pragma unroll
-                            for (int m = 0; m < 4 * ((NF + 4) / 4); m++) v[m] = 0.0f;
+                            for (int m = 0; m < 4 * GF; m++) v[m] = 0.0f;
 #pragma unroll
                             for (int o = 0; o < NF; o++) v[o] = fa[o * lda + base + k];
                             v[NF] = rec4[base + k].w;
 #pragma unroll
-                            for (int g = 0; g < (NF + 4) / 4; g++)
-                                sv[g * kTile + k] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                            for (int g = 0; g < GF; g++)
+                                st[g * kTile + k] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
                         }
                     }
                     __syncthreads();
-                    if (HH && SS && gz)
-                        tile_far_tensor<NY, HH, SS, TPT, M, HH && SS>(sX + p0, sY, sZ, sv, np, tx, ty, tz, nc, hi, lo,
-                                                                      kp);
+                    if (GZOK && gz)
+                        tile_far_tensor<NY, HH, SS, TPT, M, GZOK>(sX + p0, sY, sZ, st, np, ntx, nty, ntz, nc, hi, lo,
+                                                                  kp);
                     else
-                        tile_far_tensor<NY, HH, SS, TPT, M, false>(sX + p0, sY, sZ, sv, np, tx, ty, tz, nc, hi, lo, kp);
+                        tile_far_tensor<NY, HH, SS, TPT, M, false>(sX + p0, sY, sZ, st, np, ntx, nty, ntz, nc, hi, lo,
+                                                                   kp);
                 }
                 continue;
             }
@@ -425,54 +510,74 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
             const int ns = min(kTile, en.src1 - s0);
             const int nk = (ns + 15) & ~15;
             __syncthreads();
+            if (far) {
 #pragma unroll
-            for (int h = 0; h < kTile / THREADS; h++) {
-                const int k = tid + h * THREADS;
-                float v[4 * G];
+                for (int h = 0; h < kTile / THREADS; h++) {
+                    const int k = tid + h * THREADS;
+                    float v[4 * G];
 #pragma unroll
-                for (int m = 0; m < 4 * G; m++) v[m] = 0.0f;
-                if (k < ns) {
-                    float4 r = rec4[s0 + k];
-                    if (far) {
+                    for (int m = 0; m < 4 * G; m++) v[m] = 0.0f;
+                    if (k < ns) {
                         // proxy = cluster center + delta; one rounding to float32
+                        float4 r = rec4[s0 + k];
                         r.x = (float)((double)r.x + ox);
                         r.y = (float)((double)r.y + oy);
                         r.z = (float)((double)r.z + oz);
-                    } else {
-                        // point = leaf center + (delta_hi + delta_lo); one rounding
-                        const float4 rl = rec4lo[s0 + k];
-                        r.x = (float)(((double)r.x + (double)rl.x) + ox);
-                        r.y = (float)(((double)r.y + (double)rl.y) + oy);
-                        r.z = (float)(((double)r.z + (double)rl.z) + oz);
-                        v[2 * NF] = rl.w;  // low part of the weight
+                        srec[k] = r;
 #pragma unroll
-                        for (int o = 0; o < NF; o++) v[NF + o] = fb[o * ldb + s0 + k];
+                        for (int o = 0; o < NF; o++) v[o] = fa[o * lda + s0 + k];
+                    } else if (k < nk) {
+                        // padding record: far away, zero weight and values -> contributes 0
+                        srec[k] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
                     }
-                    srec[k] = r;
+                    if (k < nk)
 #pragma unroll
-                    for (int o = 0; o < NF; o++) v[o] = fa[o * lda + s0 + k];
-                } else if (k < nk) {
-                    // padding record: far away, zero weight and values -> contributes 0
-                    srec[k] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+                        for (int g = 0; g < G; g++)
+                            sv[g * kTile + k] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
                 }
-                if (k < nk)
+            } else {
 #pragma unroll
-                    for (int g = 0; g < G; g++)
-                        sv[g * kTile + k] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                for (int h = 0; h < kTile / THREADS; h++) {
+                    const int k = tid + h * THREADS;
+                    float v[2 * NV4];  // x y z w_hi w_lo fh[NF] fl[NF], then padding
+#pragma unroll
+                    for (int m = 0; m < 2 * NV4; m++) v[m] = 0.0f;
+                    if (k < ns) {
+                        // point = leaf center + (delta_hi + delta_lo); one rounding
+                        const float4 r = rec4[s0 + k];
+                        const float4 rl = rec4lo[s0 + k];
+                        v[0] = (float)(((double)r.x + (double)rl.x) + ox);
+                        v[1] = (float)(((double)r.y + (double)rl.y) + oy);
+                        v[2] = (float)(((double)r.z + (double)rl.z) + oz);
+                        v[3] = r.w;   // weight, high part
+                        v[4] = rl.w;  // weight, low part
+#pragma unroll
+                        for (int o = 0; o < NF; o++) {
+                            v[5 + o] = fa[o * lda + s0 + k];
+                            v[5 + NF + o] = fb[o * ldb + s0 + k];
+                        }
+                    } else if (k < nk) {
+                        // padding record: far away, zero weight and values -> contributes 0
+                        v[0] = v[1] = v[2] = 1e18f;
+                    }
+                    if (k < nk)
+#pragma unroll
+                        for (int g = 0; g < NV4; g++)
+                            sn[g * kTile + k] = make_float4(v[2 * g], v[2 * g], v[2 * g + 1], v[2 * g + 1]);
+                }
             }
             __syncthreads();
-            constexpr bool G = HH && SS;  // a Gaussian to leave out exists
             if (far) {
-                if (G && gz)
-                    tile_far<NY, HH, SS, TPT, G>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+                if (GZOK && gz)
+                    tile_far<NY, HH, SS, TPT, GZOK>(srec, sv, nk, ntx, nty, ntz, nc, hi, lo, kp);
                 else
-                    tile_far<NY, HH, SS, TPT, false>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+                    tile_far<NY, HH, SS, TPT, false>(srec, sv, nk, ntx, nty, ntz, nc, hi, lo, kp);
             } else if (self) {
-                tile_near<NY, HH, SS, true, TPT, false>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
-            } else if (G && gz) {
-                tile_near<NY, HH, SS, false, TPT, G>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+                tile_near<NY, HH, SS, true, TPT, false>(sn, nk, ntx, nty, ntz, nc, hi, lo, kp2);
+            } else if (GZOK && gz) {
+                tile_near<NY, HH, SS, false, TPT, GZOK>(sn, nk, ntx, nty, ntz, nc, hi, lo, kp2);
             } else {
-                tile_near<NY, HH, SS, false, TPT, false>(srec, sv, nk, tx, ty, tz, nc, hi, lo, kp);
+                tile_near<NY, HH, SS, false, TPT, false>(sn, nk, ntx, nty, ntz, nc, hi, lo, kp2);
             }
         }
     }
