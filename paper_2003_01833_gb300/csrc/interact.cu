@@ -13,11 +13,11 @@
 // 1/(4 pi) of G_k are added by the epilogue.
 //
 // FP32C kernel: all fields of a call (each Yukawa field with its own k, plus
-// the Hartree field) share one pass over the geometry.  Targets are held in
-// pairs, and the near field runs on two targets per instruction with the
-// packed f32x2 FMA/add/multiply (same rounding per lane as scalar code).  Each CTA owns up to
-// 256 targets of one batch (64 threads x 4 targets, or 128 x 2 for launches
-// with more than 4 fields) and a contiguous segment
+// the Hartree field) share one pass over the geometry.  Each thread holds a
+// pair of targets, and the near field and the tensor-grid far field run on
+// both with the packed f32x2 FMA/add/multiply (same rounding per lane as
+// scalar code).  Each CTA owns up to 256 targets of one batch (128 threads x
+// 2 targets) and a contiguous segment
 // of the batch's interaction list; source tiles of 256 records are staged in
 // shared memory with positions shifted from the record's frame (its leaf or
 // cluster center) to the batch center in float64 and rounded once.  Near-field
@@ -52,11 +52,13 @@ namespace tagi {
 namespace {
 
 constexpr int kTile = 256;
-// targets per thread: 4 for launches with at most 4 fields, 2 above (register
-// pressure); the CTA always owns kTargetsPerItem targets
+// targets per thread: 2 (one f32x2 pair), 128 threads per CTA.  Measured
+// against 4 targets per thread (64 threads, 122-128 registers): more warps
+// per SM hide the MUFU latency better than the extra reuse of staged values
+// per thread buys.  The CTA always owns kTargetsPerItem targets.
 template <int NF>
 struct Tpt {
-    static constexpr int value = NF <= 4 ? 4 : 2;
+    static constexpr int value = 2;
     static constexpr int threads = kTargetsPerItem / value;
 };
 constexpr int kThreads64 = 256;
@@ -196,87 +198,6 @@ __device__ __forceinline__ void tile_far(const float4* __restrict__ srec, const 
     }
 }
 
-// Far field on the tensor grid of one cluster's proxies (M nodes per
-// dimension): proxy (k1, k2, k3) sits at (X[k1], Y[k2], Z[k3]) relative to the
-// batch center, each coordinate rounded once to float32 exactly as the record
-// path rounds it, so r^2 = ((X - tx)^2 + (Y - ty)^2) + (Z - tz)^2 costs one
-// subtraction and one FMA per pair once the (k1, k2) part is formed; the
-// node coordinates are read from shared memory (broadcast).  The tile holds
-// whole k1-planes; sv holds per proxy q^ for the fields and w^ in component
-// NF.  Every row of M proxies is folded into the two-float sums.
-template <int NY, bool HH, bool SS, int TPT, int M, bool GZ>
-__device__ __forceinline__ void tile_far_tensor(const float* __restrict__ sX, const float* __restrict__ sY,
-                                                const float* __restrict__ sZ, const float4* __restrict__ sv, int np,
-                                                const float2 (&ntx)[TPT / 2], const float2 (&nty)[TPT / 2],
-                                                const float2 (&ntz)[TPT / 2], const float2 (&nc)[TPT / 2][NY + HH],
-                                                float (&hi)[TPT][NY + HH], float (&lo)[TPT][NY + HH],
-                                                const KParams& kp)
-{
-    constexpr int NF = NY + HH;
-    constexpr int GF = (NF + 4) / 4;  // float4 groups of (q^..., w^)
-    for (int pl = 0; pl < np; pl++) {
-        float dx2[TPT];
-#pragma unroll
-        for (int j = 0; j < TPT; j++) {
-            const float d = sX[pl] + lane(ntx[j >> 1], j);
-            dx2[j] = d * d;
-        }
-        for (int k2 = 0; k2 < M; k2++) {
-            float a[TPT];
-            const float yk = sY[k2];
-#pragma unroll
-            for (int j = 0; j < TPT; j++) {
-                const float d = yk + lane(nty[j >> 1], j);
-                a[j] = fmaf(d, d, dx2[j]);
-            }
-            float acc[TPT][NF];
-#pragma unroll
-            for (int j = 0; j < TPT; j++)
-#pragma unroll
-                for (int o = 0; o < NF; o++) acc[j][o] = 0.0f;
-            const float4* row = sv + (pl * M + k2) * M;
-            // partial unroll: measured fastest (full unroll leaves MUFU latency exposed)
-#pragma unroll 3
-            for (int k3 = 0; k3 < M; k3++) {
-                float qv[4 * GF];
-#pragma unroll
-                for (int g = 0; g < GF; g++) {
-                    const float4 t = row[g * kTile + k3];
-                    qv[4 * g] = t.x;
-                    qv[4 * g + 1] = t.y;
-                    qv[4 * g + 2] = t.z;
-                    qv[4 * g + 3] = t.w;
-                }
-                const float w = qv[NF];
-#pragma unroll
-                for (int j = 0; j < TPT; j++) {
-                    const float dz = sZ[k3] + lane(ntz[j >> 1], j);
-                    const float r2 = fmaf(dz, dz, a[j]);
-                    const float ri = rsqrt_approx(r2);
-                    const float r = r2 * ri;
-#pragma unroll
-                    for (int o = 0; o < NY; o++) {
-                        const float e = ex2_approx(kp.ky[o] * r);
-                        const float d = SS ? fmaf(lane(nc[j >> 1][o], j), w, qv[o]) : qv[o];
-                        acc[j][o] = fmaf(e * ri, d, acc[j][o]);
-                    }
-                    if (HH) {
-                        float d;
-                        if (SS && !GZ) {
-                            const float g = ex2_approx(kp.ga * r2);
-                            d = fmaf(lane(nc[j >> 1][NY], j) * w, g, qv[NY]);
-                        } else {
-                            d = qv[NY];
-                        }
-                        acc[j][NY] = fmaf(ri, d, acc[j][NY]);
-                    }
-                }
-            }
-            fold<NF, TPT>(acc, hi, lo);
-        }
-    }
-}
-
 // Shared layout of a staged near-field tile: per source the float2 values
 // x, y, z, w_hi, w_lo, fh[NF], fl[NF], each duplicated into both lanes, packed
 // two to a float4.
@@ -308,6 +229,96 @@ __device__ __forceinline__ void fold2(float2 (&acc)[TPT / 2][NF], float (&hi)[TP
         }
 }
 
+// Far field on the tensor grid of one cluster's proxies (M nodes per
+// dimension): proxy (k1, k2, k3) sits at (X[k1], Y[k2], Z[k3]) relative to the
+// batch center, each coordinate rounded once to float32 exactly as the record
+// path rounds it, so r^2 = ((X - tx)^2 + (Y - ty)^2) + (Z - tz)^2 costs one
+// subtraction and one FMA per pair once the (k1, k2) part is formed.  Two
+// targets per instruction (f32x2, same rounding per lane as scalar code); the
+// tile holds whole k1-planes, and per proxy the values q^ of the fields and w^
+// (component NF) duplicated into both lanes, TensorLayout<NF>::GF2 float4
+// each; sZ2 holds Z duplicated.  Every row of M proxies is folded into the
+// two-float sums.
+template <int NF>
+struct TensorLayout {
+    static constexpr int GF2 = (NF + 2) / 2;  // float4 per proxy: NF + 1 duplicated values
+};
+
+template <int NY, bool HH, bool SS, int TPT, int M, bool GZ>
+__device__ __forceinline__ void tile_far_tensor(const float* __restrict__ sX, const float* __restrict__ sY,
+                                                const float2* __restrict__ sZ2, const float4* __restrict__ st, int np,
+                                                const float2 (&ntx)[TPT / 2], const float2 (&nty)[TPT / 2],
+                                                const float2 (&ntz)[TPT / 2], const float2 (&nc)[TPT / 2][NY + HH],
+                                                float (&hi)[TPT][NY + HH], float (&lo)[TPT][NY + HH],
+                                                const KParams2& kp)
+{
+    constexpr int NF = NY + HH;
+    constexpr int NP = TPT / 2;
+    constexpr int GF2 = TensorLayout<NF>::GF2;
+    for (int pl = 0; pl < np; pl++) {
+        float2 dx2[NP];
+        const float xk = sX[pl];
+#pragma unroll
+        for (int j = 0; j < NP; j++) {
+            const float2 d = add2(make_float2(xk, xk), ntx[j]);
+            dx2[j] = mul2(d, d);
+        }
+        for (int k2 = 0; k2 < M; k2++) {
+            float2 a[NP];
+            const float yk = sY[k2];
+#pragma unroll
+            for (int j = 0; j < NP; j++) {
+                const float2 d = add2(make_float2(yk, yk), nty[j]);
+                a[j] = fma2(d, d, dx2[j]);
+            }
+            float2 acc[NP][NF];
+#pragma unroll
+            for (int j = 0; j < NP; j++)
+#pragma unroll
+                for (int o = 0; o < NF; o++) acc[j][o] = make_float2(0.0f, 0.0f);
+            const float4* row = st + (pl * M + k2) * M;
+#pragma unroll
+            for (int k3 = 0; k3 < M; k3++) {
+                float2 q[2 * GF2];  // q^ of the fields, then w^ at NF
+#pragma unroll
+                for (int g = 0; g < GF2; g++) {
+                    const float4 t = row[g * kTile + k3];
+                    q[2 * g] = make_float2(t.x, t.y);
+                    q[2 * g + 1] = make_float2(t.z, t.w);
+                }
+                const float2 w = q[NF];
+                const float2 z = sZ2[k3];
+#pragma unroll
+                for (int j = 0; j < NP; j++) {
+                    const float2 dz = add2(z, ntz[j]);
+                    const float2 r2 = fma2(dz, dz, a[j]);
+                    const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                    const float2 r = mul2(r2, ri);
+#pragma unroll
+                    for (int o = 0; o < NY; o++) {
+                        const float2 t = mul2(kp.ky[o], r);
+                        const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+                        const float2 d = SS ? fma2(nc[j][o], w, q[o]) : q[o];
+                        acc[j][o] = fma2(mul2(e, ri), d, acc[j][o]);
+                    }
+                    if (HH) {
+                        float2 d;
+                        if (SS && !GZ) {
+                            const float2 t = mul2(kp.ga, r2);
+                            const float2 g = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+                            d = fma2(mul2(nc[j][NY], w), g, q[NY]);
+                        } else {
+                            d = q[NY];
+                        }
+                        acc[j][NY] = fma2(ri, d, acc[j][NY]);
+                    }
+                }
+            }
+            fold2<NF, TPT>(acc, hi, lo);
+        }
+    }
+}
+
 // Near field: mesh points with positions relative to the batch center and
 // two-float field values f = fh + fl and weights w = wh + wl.  The SS
 // difference (fh_j - c_i) + fl_j, with c_i = fh_i, is exact up to one rounding
@@ -331,7 +342,7 @@ __device__ __forceinline__ void tile_near(const float4* __restrict__ sn, int nk,
         for (int j = 0; j < NP; j++)
 #pragma unroll
             for (int o = 0; o < NF; o++) acc[j][o] = make_float2(0.0f, 0.0f);
-#pragma unroll 2
+#pragma unroll 4
         for (int k = k0; k < k0 + kFold; k++) {
             float2 v[2 * NV4];  // 0 x, 1 y, 2 z, 3 w_hi, 4 w_lo, 5 + o fh, 5 + NF + o fl
 #pragma unroll
@@ -390,13 +401,12 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
 {
     constexpr int NF = NY + HH;
     constexpr int G = TileLayout<NF>::G;
-    constexpr int GF = (NF + 4) / 4;
     constexpr int NV4 = NearLayout<NF>::NV4;
     constexpr int TPT = Tpt<NF>::value;
     constexpr int NP = TPT / 2;
     constexpr int THREADS = Tpt<NF>::threads;
     constexpr int SB = NV4 > 1 + G ? NV4 : 1 + G;  // float4 per staged source, largest layout
-    static_assert(GF <= SB, "tensor layout fits");
+    static_assert(TensorLayout<NF>::GF2 <= SB, "tensor layout fits");
     // exponent factors of this launch's fields, from device memory so that a
     // captured graph picks up the current eigenvalues on every replay
     KParams kp{};
@@ -465,7 +475,9 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
             if (far) {
                 // proxies k = (k1 M + k2) M + k3 of this cluster: records src0 + k
                 constexpr int PL = kTile / (M * M);  // k1-planes per tile
-                __shared__ float sX[M], sY[M], sZ[M];
+                constexpr int GF2 = TensorLayout<NF>::GF2;
+                __shared__ float sX[M], sY[M];
+                __shared__ float2 sZ2[M];
                 __syncthreads();
                 if (tid < M) {
                     const float4 rx = rec4[en.src0 + tid * M * M];
@@ -473,7 +485,8 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
                     const float4 rz = rec4[en.src0 + tid];
                     sX[tid] = (float)((double)rx.x + ox);
                     sY[tid] = (float)((double)ry.y + oy);
-                    sZ[tid] = (float)((double)rz.z + oz);
+                    const float z = (float)((double)rz.z + oz);
+                    sZ2[tid] = make_float2(z, z);
                 }
                 for (int p0 = 0; p0 < M; p0 += PL) {
                     const int np = min(PL, M - p0);
@@ -484,24 +497,24 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
                     for (int h = 0; h < kTile / THREADS; h++) {
                         const int k = tid + h * THREADS;
                         if (k < nk) {
-                            float v[4 * GF];
+                            float v[2 * GF2];
 #pragma unroll
-                            for (int m = 0; m < 4 * GF; m++) v[m] = 0.0f;
+                            for (int m = 0; m < 2 * GF2; m++) v[m] = 0.0f;
 #pragma unroll
                             for (int o = 0; o < NF; o++) v[o] = fa[o * lda + base + k];
                             v[NF] = rec4[base + k].w;
 #pragma unroll
-                            for (int g = 0; g < GF; g++)
-                                st[g * kTile + k] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                            for (int g = 0; g < GF2; g++)
+                                st[g * kTile + k] = make_float4(v[2 * g], v[2 * g], v[2 * g + 1], v[2 * g + 1]);
                         }
                     }
                     __syncthreads();
                     if (GZOK && gz)
-                        tile_far_tensor<NY, HH, SS, TPT, M, GZOK>(sX + p0, sY, sZ, st, np, ntx, nty, ntz, nc, hi, lo,
-                                                                  kp);
+                        tile_far_tensor<NY, HH, SS, TPT, M, GZOK>(sX + p0, sY, sZ2, st, np, ntx, nty, ntz, nc, hi, lo,
+                                                                  kp2);
                     else
-                        tile_far_tensor<NY, HH, SS, TPT, M, false>(sX + p0, sY, sZ, st, np, ntx, nty, ntz, nc, hi, lo,
-                                                                   kp);
+                        tile_far_tensor<NY, HH, SS, TPT, M, false>(sX + p0, sY, sZ2, st, np, ntx, nty, ntz, nc, hi, lo,
+                                                                   kp2);
                 }
                 continue;
             }
