@@ -304,8 +304,9 @@ def graph_replay(T, args, wl, xyz, w, params, veff, rho, vh, psi0, flush, inter,
         T.tagi_green_graph_check(g)
         T.tagi_green_graph_destroy(g)
         T.tagi_tree_destroy(h)
-    ms = float(np.mean(times))
-    return {"ms_per_green_iteration": ms, "interactions_per_s": inter / (ms * 1e-3),
+    ms = float(np.median(times))
+    return {"ms_per_green_iteration": ms, "interactions_per_s": inter / (ms * 1e-3), "replays": len(times),
+            "statistic": "median of the timed replays (CUDA events, L2 flushed before each)",
             "note": "tree built once; each replay is one whole Green iteration (a3-a8) from a CUDA graph"}
 
 

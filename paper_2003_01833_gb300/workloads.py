@@ -106,19 +106,25 @@ ATOM_Z = {"H": 1, "Li": 3, "C": 6, "O": 8}
 def _shells(sym: str):
     """Occupied shells of the neutral atom: list of (kind, occ, Z).
 
-    kind is '1s', '2s' or '2p'; the radial shapes are hydrogenic with the bare
-    nuclear charge, the stand-in the Li workload specifies (1s ~ e^{-Zr},
-    2s ~ (2 - Zr) e^{-Zr/2}); 2p ~ r e^{-Zr/2}.
+    kind is '1s', '2s' or '2p'; the radial shapes are hydrogenic (1s ~ e^{-Zr},
+    2s ~ (2 - Zr) e^{-Zr/2}, 2p ~ r e^{-Zr/2}) with the bare nuclear charge for
+    H and Li (the stand-in the Li workload specifies) and Slater-screened
+    effective charges for C and O.
     """
     Z = ATOM_Z[sym]
     if sym == "H":
         return [("1s", 1.0, Z)]
     if sym == "Li":
         return [("1s", 2.0, Z), ("2s", 1.0, Z)]
+    # C and O: effective charges from Slater's screening rules (1s: Z - 0.30;
+    # n = 2: Z - 0.35 per other n = 2 electron - 0.85 per 1s electron).  With
+    # bare charges their stand-in density is so compact that the initial
+    # Hartree potential screens the nuclei almost completely and binds no
+    # valence level.
     if sym == "C":
-        return [("1s", 2.0, Z), ("2s", 2.0, Z), ("2p", 2.0, Z)]
+        return [("1s", 2.0, 5.70), ("2s", 2.0, 3.25), ("2p", 2.0, 3.25)]
     if sym == "O":
-        return [("1s", 2.0, Z), ("2s", 2.0, Z), ("2p", 4.0, Z)]
+        return [("1s", 2.0, 7.70), ("2s", 2.0, 4.55), ("2p", 4.0, 4.55)]
     raise ValueError(sym)
 
 
@@ -511,6 +517,50 @@ def carbon_monoxide(seed: int = 2, tol_m: float = 1e-8, p: int = 4, half_width: 
     mol = Molecule(["C", "O"], np.array([[-1.06581, 0.0, 0.0], [1.06581, 0.0, 0.0]]))
     mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
     return _molecule_workload("CO", mol, mesh, seed, n_orb)
+
+
+def carbon_monoxide_scf(tol_m: float = 3e-7, p: int = 4, half_width: float = 20.0,
+                        uniform_levels: int = 3) -> Workload:
+    """CO for an SCF run from an aufbau-style start: 8 orbitals (7 doubly
+    occupied and the 2pi* virtual, N_w = 8 as in Section 6), built from the
+    Slater-screened atomic orbitals in energy order and orthonormalised in
+    that order: O 1s, C 1s, 3sigma (2s of both), 4sigma (2p along the bond),
+    1pi (2p_y and 2p_z), 5sigma (carbon 2s - 2p lone pair), 2pi* (O - C 2p_y),
+    with the atomic LDA-like eigenvalues as guesses.  The bond lies on x.
+    V_shift = -1.5: a deeper gauge shift (Eq. gauge-shift leaves the
+    eigenproblem unchanged) keeps eps + V_shift < 0 through the first
+    gradient-free updates from this crude start.  The tol_m = 3e-7 mesh has
+    638,500 points (the paper's CO mesh at this tolerance: 661,625)."""
+    mol = Molecule(["C", "O"], np.array([[-1.06581, 0.0, 0.0], [1.06581, 0.0, 0.0]]))
+    mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
+    pts = mesh.xyz.T
+    C, O = mol.pos[0], mol.pos[1]
+    (_, _, zc1), (_, _, zc2), _ = _shells("C")
+    (_, _, zo1), (_, _, zo2), _ = _shells("O")
+
+    def ao(kind, Z, R, d=None):
+        r = _dist(pts, R)
+        f = radial_orbital(kind, Z, r)
+        return f if d is None else f * (pts[:, d] - R[d]) / np.maximum(r, 1e-300)
+
+    basis = [ao("1s", zo1, O), ao("1s", zc1, C), ao("2s", zo2, O) + ao("2s", zc2, C),
+             ao("2p", zo2, O, 0) - ao("2p", zc2, C, 0), ao("2p", zo2, O, 1) + ao("2p", zc2, C, 1),
+             ao("2p", zo2, O, 2) + ao("2p", zc2, C, 2), ao("2s", zc2, C) - ao("2p", zc2, C, 0),
+             ao("2p", zo2, O, 1) - ao("2p", zc2, C, 1)]
+    w = mesh.w
+    q = []
+    for v in basis:
+        v = v.copy()
+        for u in q:
+            v -= np.sum(v * u * w) * u
+        q.append(v / np.sqrt(np.sum(v * v * w)))
+    rho = density0(mol, pts)
+    vx = v_ext(mol, pts)
+    veff = vx + v_hartree0(mol, pts) + lda_xc(rho)[1]
+    eps = np.array([-18.8, -9.9, -1.0, -0.5, -0.45, -0.45, -0.35, -0.1])
+    return Workload(name="CO", mesh=mesh, veff=veff, psi=np.array(q), eps=eps, rho=rho, vshift=-1.5, theta=0.7,
+                    degree=8, leaf_size=2000, meta={"tol_m": tol_m, "start": "aufbau"}, vext=vx, n_elec=14.0,
+                    e_zz=nuclear_repulsion(mol))
 
 
 def benzene(seed: int = 3, tol_m: float = 3e-8, p: int = 4, half_width: float = 20.0,

@@ -5,8 +5,8 @@ oracle treecode restricted to those batches (the oracle cannot afford the
 whole mesh).
 
 - Li, 309,000 points: 2 orbitals + Hartree, one launch (the benchmark's).
-- CO, 1,625,500 points (tol_m = 1e-8): 7 orbitals + Hartree, one launch.
-- C6H6, 4,694,500 points (tol_m = 3e-8): 21 orbitals + Hartree, three
+- CO, 1,719,000 points (tol_m = 1e-8): 7 orbitals + Hartree, one launch.
+- C6H6, 4,572,000 points (tol_m = 3e-8): 21 orbitals + Hartree, three
   launches (8 + 8 + 5 and the Hartree field).
 
 Tolerance: relative L2 1e-6 per checked field over the sampled targets
