@@ -89,3 +89,30 @@ def test_benzene_full_size_sampled(T):
     assert 4.4e6 < wl.n < 5.2e6 and wl.psi.shape[0] == 21
     # one field of each launch group (fields 0-7, 8-15, 16-20 + Hartree)
     _check(T, wl, [0, 10, 20], nbatch=2, seed=2)
+
+
+def test_grouping_does_not_change_any_field(T):
+    """One pass over 10 Yukawa fields and the Hartree field (launch groups
+    of 8 + 3) gives, bit for bit, what the separate Yukawa (8 + 2) and
+    Coulomb (1) calls give: every operation of the kernel is an explicit
+    intrinsic, so a field's sums do not depend on its launch group."""
+    wl = W.hydrogen_adaptive()
+    m = wl.mesh
+    rng = np.random.default_rng(7)
+    nf = 10
+    k = rng.uniform(0.8, 3.0, size=nf)
+    r = np.sqrt(np.sum(m.xyz**2, axis=0))
+    f = np.stack([np.exp(-rng.uniform(0.5, 2.0) * r) * (1 + 0.1 * np.sin(m.xyz[0] + o)) for o in range(nf)])
+    rho = np.exp(-r) / np.pi
+    with T.Tree(dev(m.xyz), dev(m.w), theta=0.7, degree=8, leaf_size=2000, prec=T.TAGI_FP32C) as tr:
+        u1 = torch.empty((nf, wl.n), dtype=torch.float64, device="cuda")
+        v1 = torch.empty(wl.n, dtype=torch.float64, device="cuda")
+        T.tagi_fields_conv(tr.handle, dev(f), list(k), u1, rho=dev(rho), vh=v1)
+        u2 = torch.empty_like(u1)
+        v2 = torch.empty_like(v1)
+        T.tagi_yukawa_conv(tr.handle, dev(f), list(k), u2)
+        T.tagi_coulomb_conv(tr.handle, dev(rho), v2)
+        v3 = torch.empty_like(v1)
+        T.tagi_fields_conv(tr.handle, None, [], None, rho=dev(rho), vh=v3)
+        assert torch.equal(u1, u2)
+        assert torch.equal(v1, v2) and torch.equal(v1, v3)
