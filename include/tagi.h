@@ -82,6 +82,7 @@ typedef struct {
     int32_t n_proxies;      /* (n+1)^3 proxies per cluster */
     int64_t near_pairs_nogauss; /* near pairs in entries whose boxes are >= sqrt(42) alpha apart */
     int64_t far_pairs_nogauss;  /* far pairs likewise: there exp(-r^2/alpha^2) <= 2^-60 */
+    int64_t ant_points;         /* sum over approximated clusters of their points (anterpolation work) */
 } tagi_tree_stats;
 
 /* Build the source-cluster tree and target batches (Algorithm 3 line 1,

@@ -43,6 +43,8 @@ def lib():
         L.oracle_direct_yukawa.argtypes = [ctypes.c_int64, _D, _D, _D, _D, ctypes.c_int64, _D, _D,
                                            _D, _D, _D, ctypes.c_double, ctypes.c_int, _D]
         L.oracle_direct_coulomb.argtypes = L.oracle_direct_yukawa.argtypes
+        L.oracle_threads.argtypes = [ctypes.c_int]
+        L.oracle_threads.restype = ctypes.c_int
         L.oracle_tree_build.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int]
         L.oracle_tree_build.restype = ctypes.c_void_p
         L.oracle_tree_free.argtypes = [ctypes.c_void_p]
@@ -62,6 +64,11 @@ def lib():
                                               ctypes.c_int, _I32, _D]
         _lib = L
     return _lib
+
+
+def threads(n: int = 0) -> int:
+    """Set the oracle's OpenMP thread count (n > 0) and return the count in use."""
+    return int(lib().oracle_threads(int(n)))
 
 
 def _p(a, t=_D):

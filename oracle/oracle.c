@@ -40,6 +40,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORACLE_PI 3.14159265358979323846
 #define ORACLE_SQRT2 1.4142135623730951
@@ -528,4 +531,18 @@ int oracle_treecode_batches(const oracle_tree* t, double theta, int degree, int 
     for (int c = 0; c < t->nc; c++) free(C0.qh[c]);
     free(C0.qh);
     return 0;
+}
+
+/* Threads of the OpenMP loops above (the benchmark times the oracle on all
+ * cores and on one); n < 1 leaves the setting alone.  Returns the count the
+ * next parallel loop will use. */
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -329,6 +329,7 @@ tagi_status tagi_tree_info(const tagi_tree* tree, tagi_tree_stats* st)
         st->n_proxies = T->P;
         st->near_pairs_nogauss = T->near_pairs_ng;
         st->far_pairs_nogauss = T->far_pairs_ng;
+        st->ant_points = T->ant_points;
     });
 }
 

@@ -151,6 +151,7 @@ struct Tree {
     int64_t nent = 0, nitems = 0, ntchunk = 0, nant = 0, nrec = 0;
     int64_t near_pairs = 0, far_pairs = 0;
     int64_t near_pairs_ng = 0, far_pairs_ng = 0;  // pairs of entries flagged bit2
+    int64_t ant_points = 0;                        // sum of N_S over approximated clusters
 
     // points in tree order
     DevBuf perm;             // int[n] tree position -> caller index

@@ -607,6 +607,14 @@ __global__ void k_ant_counts(int nfar, const int* far_cl, const int* begin, cons
     cnt[f] = (end[c] - begin[c] + kAntChunk - 1) / kAntChunk;
 }
 
+__global__ void k_far_points(int nfar, const int* far_cl, const int* begin, const int* end, int64_t* cnt)
+{
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfar) return;
+    int c = far_cl[f];
+    cnt[f] = end[c] - begin[c];
+}
+
 __global__ void k_ant_fill(int nfar, const int* far_cl, const int* begin, const int* end, const int64_t* off,
                            AntItem* items, int* far_ant0)
 {
@@ -1003,6 +1011,7 @@ void build_tree(Tree& T, const double* xyz, const double* w)
     }
 
     // ---- anterpolation items
+    T.ant_points = 0;
     if (T.nfar > 0) {
         DevBuf ac, ao;
         ac.ensure(8 * (size_t)T.nfar);
@@ -1012,8 +1021,17 @@ void build_tree(Tree& T, const double* xyz, const double* w)
         exclusive_scan_i64(ac.as<int64_t>(), ao.as<int64_t>(), T.nfar, s);
         TAGI_LAUNCH_CHECK();
         T.nant = read_i64(ao.as<int64_t>() + T.nfar, s, H);
+        // sum of N_S over approximated clusters (anterpolation work, reported by tagi_tree_info)
+        launch(k_far_points, nblocks(T.nfar, 128), 128, 0, s, T.nfar, T.far_cl.as<int>(), T.cl_begin.as<int>(),
+               T.cl_end.as<int>(), ac.as<int64_t>());
+        exclusive_scan_i64(ac.as<int64_t>(), ao.as<int64_t>(), T.nfar, s);
+        TAGI_LAUNCH_CHECK();
+        T.ant_points = read_i64(ao.as<int64_t>() + T.nfar, s, H);
         T.ant_items.ensure(sizeof(AntItem) * (size_t)T.nant);
         T.far_ant0.ensure(4 * ((size_t)T.nfar + 1));
+        launch(k_ant_counts, nblocks(T.nfar, 128), 128, 0, s, T.nfar, T.far_cl.as<int>(), T.cl_begin.as<int>(),
+                                                          T.cl_end.as<int>(), ac.as<int64_t>());
+        exclusive_scan_i64(ac.as<int64_t>(), ao.as<int64_t>(), T.nfar, s);
         launch(k_ant_fill, nblocks(T.nfar + 1, 128), 128, 0, s, T.nfar, T.far_cl.as<int>(), T.cl_begin.as<int>(),
                                                             T.cl_end.as<int>(), ao.as<int64_t>(),
                                                             T.ant_items.as<AntItem>(), T.far_ant0.as<int>());

@@ -48,7 +48,7 @@ class tagi_tree_stats(ctypes.Structure):
                 ("n_list_entries", ctypes.c_int64), ("n_items", ctypes.c_int64),
                 ("near_pairs", ctypes.c_int64), ("far_pairs", ctypes.c_int64), ("degree", ctypes.c_int32),
                 ("n_proxies", ctypes.c_int32), ("near_pairs_nogauss", ctypes.c_int64),
-                ("far_pairs_nogauss", ctypes.c_int64)]
+                ("far_pairs_nogauss", ctypes.c_int64), ("ant_points", ctypes.c_int64)]
 
 
 class tagi_gi_params(ctypes.Structure):
