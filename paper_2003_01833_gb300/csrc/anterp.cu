@@ -46,13 +46,72 @@ __device__ __forceinline__ void basis_prod(double t, bool degenerate, int n, con
     }
 }
 
+constexpr int kAntLP = 12;  // padded basis row of the cache (degree <= 11)
+static_assert(kMaxDegree + 1 <= kAntLP, "basis row fits");
+
+// Basis cache of the float32 path: for every point of every anterpolation
+// item and each dimension, the float64 basis of Eq. Lagrange_polynomials on
+// the float32-rounded nodes, rounded to float32 (exactly the values k_ant
+// evaluates), rows of kAntLP floats at ((item * kAntChunk + j) * 3 + d).
+__global__ void __launch_bounds__(kAntThreads) k_ant_basis(const AntItem* __restrict__ items,
+                                                           const double* __restrict__ px,
+                                                           const double* __restrict__ py,
+                                                           const double* __restrict__ pz,
+                                                           const double* __restrict__ lo,
+                                                           const double* __restrict__ hi, int degree,
+                                                           float* __restrict__ antL)
+{
+    __shared__ double dnodes[kMaxDegree + 1], inv[kMaxDegree + 1];
+    const AntItem it = items[blockIdx.x];
+    const int c = it.cluster;
+    double cc[3], hh[3], ih[3];
+    for (int d = 0; d < 3; d++) {
+        cc[d] = (lo[3 * c + d] + hi[3 * c + d]) * 0.5;
+        hh[d] = (hi[3 * c + d] - lo[3 * c + d]) * 0.5;
+        ih[d] = hh[d] == 0.0 ? 0.0 : 1.0 / hh[d];
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k <= degree; k++) dnodes[k] = (double)(float)cos(M_PI * k / degree);
+        for (int k = 0; k <= degree; k++) {
+            double d = 1.0;
+            for (int j = 0; j <= degree; j++)
+                if (j != k) d *= dnodes[k] - dnodes[j];
+            inv[k] = 1.0 / d;
+        }
+    }
+    __syncthreads();
+    const int np = it.p1 - it.p0;
+    for (int e = threadIdx.x; e < 3 * np; e += blockDim.x) {
+        const int j = e / 3, d = e % 3;
+        const double* x = d == 0 ? px : (d == 1 ? py : pz);
+        const bool deg = hh[d] == 0.0;
+        double Ld[kMaxDegree + 1];
+        const double td = deg ? 0.0 : (x[it.p0 + j] - cc[d]) * ih[d];
+        basis_prod(td, deg, degree, dnodes, inv, Ld);
+        float4* row = reinterpret_cast<float4*>(antL + (((size_t)blockIdx.x * kAntChunk + j) * 3 + d) * kAntLP);
+#pragma unroll
+        for (int g = 0; g < kAntLP / 4; g++) {
+            float v[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int k = 4 * g + i;
+                v[i] = k <= degree ? (float)Ld[k] : 0.0f;
+            }
+            row[g] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    }
+}
+
 // R: arithmetic type of the basis and per-tile sums; A: accumulator type.
+// antL: the basis rows of every point of every item (k_ant_basis), or null
+// to evaluate them here.
 template <class R, class A, int NQ>
 __global__ void __launch_bounds__(kAntThreads) k_ant(const AntItem* __restrict__ items, const double* __restrict__ px,
                                                      const double* __restrict__ py, const double* __restrict__ pz,
                                                      const double* __restrict__ lo, const double* __restrict__ hi,
                                                      int degree, int f32nodes, const R* __restrict__ q,
-                                                     int64_t ldq, double* __restrict__ part)
+                                                     int64_t ldq, double* __restrict__ part,
+                                                     const float* __restrict__ antL)
 {
     __shared__ R Ls[kAntTile][3][kMaxDegree + 1];
     __shared__ R qs[NQ][kAntTile];
@@ -98,7 +157,18 @@ __global__ void __launch_bounds__(kAntThreads) k_ant(const AntItem* __restrict__
         if (threadIdx.x < 3 * kAntTile) {
             int j = threadIdx.x / 3, d = threadIdx.x % 3;
             R L[kMaxDegree + 1];
-            if (j < nt) {
+            if (j < nt && antL) {
+                const float4* row = reinterpret_cast<const float4*>(
+                    antL + (((size_t)blockIdx.x * kAntChunk + (p0 - it.p0) + j) * 3 + d) * kAntLP);
+#pragma unroll
+                for (int g = 0; g < kAntLP / 4; g++) {
+                    const float4 v = row[g];
+                    if (4 * g <= degree) L[4 * g] = (R)v.x;
+                    if (4 * g + 1 <= degree) L[4 * g + 1] = (R)v.y;
+                    if (4 * g + 2 <= degree) L[4 * g + 2] = (R)v.z;
+                    if (4 * g + 3 <= degree) L[4 * g + 3] = (R)v.w;
+                }
+            } else if (j < nt) {
                 const double* x = d == 0 ? px : (d == 1 ? py : pz);
                 bool deg = hh[d] == 0.0;
                 // the basis on [-1, 1], evaluated in
@@ -193,13 +263,13 @@ __global__ void k_split_w(const double* w, int64_t n, float* out)
 
 template <class R, class A>
 void launch_ant(int nq, int nitems, const AntItem* items, Tree& T, const R* q, int64_t ldq, double* part,
-                cudaStream_t s)
+                cudaStream_t s, const float* antL = nullptr)
 {
 #define TAGI_ANT_CASE(NQ)                                                                                   \
     case NQ:                                                                                                \
         launch(k_ant<R, A, NQ>, nitems, kAntThreads, 0, s, items, T.px.as<double>(), T.py.as<double>(),         \
                                                        T.pz.as<double>(), T.cl_lo.as<double>(),             \
-                                                       T.cl_hi.as<double>(), T.degree, T.prec == TAGI_FP32C, q, ldq, part);       \
+                                                       T.cl_hi.as<double>(), T.degree, T.prec == TAGI_FP32C, q, ldq, part, antL); \
         break;
     switch (nq) {
         TAGI_ANT_CASE(1)
@@ -224,6 +294,16 @@ void anterpolate_weights(Tree& T)
     if (T.nfar == 0) return;
     cudaStream_t s = T.stream;
     if (T.prec == TAGI_FP32C) {
+        // basis cache (kept with the tree while it fits the budget below)
+        const size_t cache_bytes = sizeof(float) * (size_t)T.nant * kAntChunk * 3 * kAntLP;
+        if (cache_bytes <= ((size_t)16 << 30)) {
+            T.antL.ensure(cache_bytes);
+            launch(k_ant_basis, (int)T.nant, kAntThreads, 0, s, T.ant_items.as<AntItem>(), T.px.as<double>(),
+                   T.py.as<double>(), T.pz.as<double>(), T.cl_lo.as<double>(), T.cl_hi.as<double>(), T.degree,
+                   T.antL.as<float>());
+            TAGI_LAUNCH_CHECK();
+        }
+        const float* antL = T.antL.p ? T.antL.as<float>() : nullptr;
         // w^ from the two-float weights (w_hi, w_lo), on the float32 nodes
         // where the proxies sit
         T.antpart.ensure(sizeof(double) * (size_t)T.nant * T.P * 2);
@@ -231,7 +311,7 @@ void anterpolate_weights(Tree& T)
         w2.ensure(sizeof(float) * 2 * (size_t)T.n);
         launch(k_split_w, (int)((T.n + 255) / 256), 256, 0, s, T.pw.as<double>(), T.n, w2.as<float>());
         launch_ant<float, double>(2, (int)T.nant, T.ant_items.as<AntItem>(), T, w2.as<float>(), T.n,
-                                  T.antpart.as<double>(), s);
+                                  T.antpart.as<double>(), s, antL);
         launch(k_ant_reduce_w, T.nfar, 256, 0, s, T.far_ant0.as<int>(), T.antpart.as<double>(), T.P, T.n,
                T.rec4.as<float4>());
         TAGI_LAUNCH_CHECK();
@@ -254,7 +334,7 @@ void anterpolate_fields32(Tree& T, int nf)
         int g = nf - g0 < 8 ? nf - g0 : 8;
         T.antpart.ensure(sizeof(double) * (size_t)T.nant * T.P * g);
         launch_ant<float, double>(g, (int)T.nant, T.ant_items.as<AntItem>(), T, T.qant.as<float>() + g0 * T.n,
-                                  T.n, T.antpart.as<double>(), s);
+                                  T.n, T.antpart.as<double>(), s, T.antL.p ? T.antL.as<float>() : nullptr);
         launch(k_ant_reduce, T.nfar, 256, 0, s, T.nfar, T.far_ant0.as<int>(), T.antpart.as<double>(), g, T.P, T.n, 0,
                                             T.fa.as<float>(), nullptr, g0, T.nrec);
         TAGI_LAUNCH_CHECK();

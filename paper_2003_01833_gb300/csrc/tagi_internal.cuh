@@ -192,6 +192,7 @@ struct Tree {
     DevBuf wc;          // double [n] quadrature weights in the caller's order
     DevBuf part;        // double partial sums
     DevBuf antpart;     // double anterpolation partials
+    DevBuf antL;        // FP32C: float32 basis rows of every anterpolation point (anterp.cu)
     DevBuf scratch;     // general scratch (reductions)
     DevBuf rates32;     // float [kMaxCallFields] exponent factors of the current call
     DevBuf rates64;     // double [kMaxCallFields] k or alpha as applied by the kernels
