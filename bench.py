@@ -45,8 +45,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the FP64 plain-form comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-loop", action="store_true", help="skip the Green Iteration loop and SCF legs")
-    ap.add_argument("--workload", default="li", choices=["li", "li-small"],
-                    help="li: the benchmark workload (309k points); li-small: tol_m 1e-3 mesh (99k) for profiling")
+    ap.add_argument("--workload", default="li", choices=["li", "li-small", "co", "c6h6"],
+                    help="li: the benchmark workload (309k points); li-small: tol_m 1e-3 mesh (99k) for "
+                         "profiling; co (1.72M points, 7 orbitals + Hartree) and c6h6 (4.57M points, 21 orbitals "
+                         "+ Hartree): the larger configurations, Green steps only")
     ap.add_argument("--profile-case", action="store_true",
                     help="build one tree and run two Green steps, nothing timed (for ncu captures)")
     return ap.parse_args()
@@ -65,6 +67,10 @@ WORKLOAD = "li"
 def make_workload(seed):
     from paper_2003_01833_gb300 import workloads as W
 
+    if WORKLOAD == "co":
+        return W.carbon_monoxide(seed=1 + seed)
+    if WORKLOAD == "c6h6":
+        return W.benzene(seed=2 + seed)
     return W.lithium(seed=seed, tol_m=1e-3) if WORKLOAD == "li-small" else W.lithium(seed=seed)
 
 
@@ -185,8 +191,20 @@ def kernel_work(info, ny, hh):
 
 def roofline(info, nfields_y, hh, kernel_ms, clk_mhz, sms):
     """ALU roofline of k_interact32: the tighter of the issue bound (128
-    instructions per SM per clock) and the MUFU bound (measured ex2 rate)."""
-    instr, xu = kernel_work(info, nfields_y, hh)
+    instructions per SM per clock) and the MUFU bound (measured ex2 rate).
+    Fields go to the kernel in launch groups of up to 8 (the Hartree field
+    joins the last group when it fits), each group with its own geometry."""
+    instr = xu = 0
+    o = 0
+    while o < nfields_y or (hh and o == nfields_y):
+        g = min(8, nfields_y - o)
+        g_hh = hh and o + g == nfields_y and g < 8
+        i1, x1 = kernel_work(info, g, g_hh)
+        instr += i1
+        xu += x1
+        o += g + (1 if g_hh else 0)
+        if g_hh or (g == 0 and not hh):
+            break
     nf = nfields_y + (1 if hh else 0)
     inter = (info["near_pairs"] + info["far_pairs"]) * nf
     f = clk_mhz * 1e6
@@ -518,8 +536,10 @@ def main():
     graph = graph_replay(T, args, wl, xyz, w, params, veff, rho, vh, psi0, flush, inter, dev) if rank == 0 else None
 
     # ---- Green Iteration to convergence (fixed V_eff), with and without mixing
-    loop = gi_loop(T, wl, xyz, w, params, veff, psi0) if (rank == 0 and not args.no_loop) else None
+    loop = gi_loop(T, wl, xyz, w, params, veff, psi0) if (rank == 0 and not args.no_loop and
+                                                          WORKLOAD in ("li", "li-small")) else None
     scf = scf_loop(T, wl, xyz, w, params) if (rank == 0 and not args.no_loop and WORKLOAD == "li") else None
+    lithium = WORKLOAD in ("li", "li-small")  # the other workloads time Green steps only
 
     # ---- end to end through the public API: pinned host inputs -> device,
     # step, results -> host, all inside the timed region
@@ -553,7 +573,7 @@ def main():
 
     # ---- plain FP64 form: one orbital per launch, same tree, no graph
     plain = None
-    if not args.no_plain and rank == 0:
+    if not args.no_plain and rank == 0 and lithium:
         pp = T.make_params(theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size, prec=T.TAGI_FP64)
         psi64 = psi0.clone()
         torch.cuda.synchronize()
@@ -585,7 +605,7 @@ def main():
     clk_mhz = clk.get("sm_mhz") or 1900.0
     achieved, peak, bounds = roofline(info, nw, True, k_ms_per_step, clk_mhz, sms)
     cpu = None
-    if not args.no_cpu:
+    if not args.no_cpu and lithium:
         rate, threads, desc, _ = cpu_oracle_rate(wl, budget_s=20.0)
         rate1, _, desc1, _ = cpu_oracle_rate(wl, budget_s=6.0, seed=1, nthreads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
@@ -594,7 +614,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
-        "config": {"workload": f"Li atom (hydrogenic Z=3, adaptive mesh p=4, tol_m 3e-7): {n} points, "
+        "config": {"workload": (f"Li atom (hydrogenic Z=3, adaptive mesh p=4, tol_m 3e-7): {n} points, "
+                                if WORKLOAD == "li" else f"{wl.name}, adaptive mesh p=4: {n} points, ") +
                                f"{nw} orbitals + Hartree, degree {wl.degree}, theta {wl.theta}, leaf {wl.leaf_size}",
                    "step": "tree+lists+items, fields, anterpolation, near/far kernel, SS epilogue, "
                            "eps update, MGS, residuals, E_H",
@@ -603,9 +624,9 @@ def main():
         "s_per_green_iteration": t_max * 1e-3,
         "phases_ms_per_step": {g: prof[g][0] / max(1, args.steps) for g in prof},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "interactions/s",
-                     "frac": achieved / peak, "traffic": kernel_traffic(),
+                     "frac": achieved / peak, "traffic": kernel_traffic() if WORKLOAD == "li" else None,
                      "kernel": "k_interact32 (near/far)", **bounds,
-                     "ncu_small_case_pct": kernel_pipes(),
+                     "ncu_small_case_pct": kernel_pipes() if lithium else None,
                      "peak_model": f"min(issue: {sms} SMs x 128 instr/clk, MUFU: {sms} SMs x "
                                    f"{XU_EX2_PER_SM_CLK} ex2/clk) x {clk_mhz:.0f} MHz (measured clock) over the "
                                    "per-interaction counts; peak of measured unit rates, not MEASURED_PEAKS.json "
