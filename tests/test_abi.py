@@ -68,3 +68,17 @@ def test_green_iterate_validation_needs_no_gpu(lib):
     assert L.tagi_green_iterate(None, None, 0.0, None, eps, 1, ctypes.byref(gp), None, None, None,
                                 None) == T.TAGI_ERR_INVALID_ARG
     assert "NULL" in T.lib().tagi_last_error().decode()
+
+
+def test_new_entry_points_validate_without_gpu(lib):
+    import paper_2003_01833_gb300.tagi as T
+
+    L = T.lib()
+    k = (ctypes.c_double * 1)(1.0)
+    assert L.tagi_fields_conv(None, None, k, 1, None, None, None, None) == T.TAGI_ERR_INVALID_ARG
+    p = T.tagi_scf_params(3.0, 6.3e-4, 0.0, 0.5, 5, 3e-3, 1e-5, 4, 100, 0.5, 5, float("inf"))
+    h = ctypes.c_void_p()
+    assert L.tagi_scf_create(None, ctypes.byref(p), ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+    eps = (ctypes.c_double * 1)(-0.5)
+    assert L.tagi_scf_step(None, None, 0.0, None, None, eps, 1, None, None, None, None) == T.TAGI_ERR_INVALID_ARG
+    assert L.tagi_scf_destroy(None) == T.TAGI_OK
