@@ -214,18 +214,28 @@ struct KParams2 {
 };
 
 // Fold of pair accumulators: lane x of pair i belongs to target 2i, lane y
-// to target 2i+1; the same TwoSum as fold().
+// to target 2i+1.  The TwoSum of fold() on both lanes at once: each
+// difference x - y is fma(y, -1, x), one rounding as in the scalar form, so
+// the result is bit for bit that of two_sum.
 template <int NF, int TPT>
 __device__ __forceinline__ void fold2(float2 (&acc)[TPT / 2][NF], float (&hi)[TPT][NF], float (&lo)[TPT][NF])
 {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-    for (int j = 0; j < TPT; j++)
+    for (int i = 0; i < TPT / 2; i++)
 #pragma unroll
         for (int o = 0; o < NF; o++) {
-            float sum, er;
-            two_sum(hi[j][o], lane(acc[j >> 1][o], j), sum, er);
-            hi[j][o] = sum;
-            lo[j][o] += er;
+            const float2 a = make_float2(hi[2 * i][o], hi[2 * i + 1][o]);
+            const float2 b = acc[i][o];
+            const float2 s = add2(a, b);
+            const float2 bp = fma2(a, m1, s);                        // s - a
+            const float2 ap = fma2(bp, m1, s);                       // s - bp
+            const float2 e = add2(fma2(ap, m1, a), fma2(bp, m1, b));  // (a - ap) + (b - bp)
+            const float2 l = add2(make_float2(lo[2 * i][o], lo[2 * i + 1][o]), e);
+            hi[2 * i][o] = s.x;
+            hi[2 * i + 1][o] = s.y;
+            lo[2 * i][o] = l.x;
+            lo[2 * i + 1][o] = l.y;
         }
 }
 
