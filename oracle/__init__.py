@@ -292,7 +292,7 @@ def anderson_mix(X, F, beta, wx):
 
 
 def green_iterate(tree, theta, degree, w, veff, vshift, psi, eps, tol_gi, max_iter, beta=0.5, history=5,
-                  mix_tol=np.inf):
+                  mix_tol=np.inf, store_output=False):
     """Green Iteration for all orbitals at once (Algorithm 2, batched as in
     green_step), with Anderson mixing of each eigenpair x = (eps, psi) under
     (x1, x2) = eps1 eps2 + sum psi1 psi2 w (Section 4.3).
@@ -304,7 +304,10 @@ def green_iterate(tree, theta, degree, w, veff, vshift, psi, eps, tol_gi, max_it
         orbital (the new iterate of an active one, the stored pair of a
         converged one) and normalise: g(x) = (eps', psi');
       line 7: r = ||psi' - psi||_w.  If r < tol_gi the orbital is converged and
-        keeps its step input (eps^(n), psi^(n)), as Algorithm 2 stores it.
+        keeps its step input (eps^(n), psi^(n)), as Algorithm 2 stores it, or,
+        with store_output, the step's output g(x) = (eps^(n+1), psi^(n+1)):
+        inside an SCF iteration the stored input stops following V_eff once
+        its change moves the orbital by less than tol_gi in one step.
     Otherwise the next input is g(x), or, once the orbital's residual has
     fallen below mix_tol (mixing stays on from then), the Anderson update of
     its last history+1 pairs (x_j, F_j = g(x_j) - x_j) with parameter beta.
@@ -355,6 +358,8 @@ def green_iterate(tree, theta, degree, w, veff, vshift, psi, eps, tol_gi, max_it
             if resid[o] < tol_gi:
                 conv[o] = True
                 iters[o] = step + 1
+                if store_output:
+                    eps[o], psi[o] = e_new[o], q[o]
                 continue
             if resid[o] < mix_tol:
                 mixing[o] = True
@@ -429,12 +434,14 @@ def lda_xc(rho):
 def fermi_level(eps, n_elec, kT):
     """Fermi energy mu with 2 sum_i f(eps_i, mu) = N_e and
     f = 1 / (e^{(eps - mu)/kT} + 1) (Eq. Fermi, density-construction), by
-    bisection to the resolution of float64.  Returns (mu, f)."""
+    bisection to the resolution of float64.  N_e = 2 N_w fills every state:
+    the bisection then ends where every f rounds to 1 (the mu -> infinity
+    limit).  Returns (mu, f)."""
     import scipy.special
 
     eps = np.asarray(eps, np.float64)
-    if not (0.0 < n_elec < 2.0 * eps.size and kT > 0.0):
-        raise ValueError("need 0 < N_e < 2 N_w and kT > 0")
+    if not (0.0 < n_elec <= 2.0 * eps.size and kT > 0.0):
+        raise ValueError("need 0 < N_e <= 2 N_w and kT > 0")
     occ = lambda mu: scipy.special.expit((mu - eps) / kT)
     lo, hi = eps.min() - 60.0 * kT, eps.max() + 60.0 * kT
     for _ in range(400):
@@ -471,7 +478,8 @@ def scf_potentials(tree, theta, degree, w, vext, rho, alpha=1.0):
 
 
 def scf_step(tree, theta, degree, w, vext, rho_in, psi, eps, vshift, n_elec, kT, e_zz, tol_gi, max_iter,
-             mix, scf_beta=0.5, scf_history=5, gi_beta=0.5, gi_history=5, mix_tol=np.inf, alpha=1.0):
+             mix, scf_beta=0.5, scf_history=5, gi_beta=0.5, gi_history=5, mix_tol=np.inf, alpha=1.0,
+             gi_store_output=False):
     """One SCF iteration (Algorithm 1):
       line 2: V_eff[rho_in] (scf_potentials);
       line 3: eigenpairs by Green Iteration with Anderson mixing
@@ -489,7 +497,7 @@ def scf_step(tree, theta, degree, w, vext, rho_in, psi, eps, vshift, n_elec, kT,
     """
     pot = scf_potentials(tree, theta, degree, w, vext, rho_in, alpha=alpha)
     gi = green_iterate(tree, theta, degree, w, pot["veff"], vshift, psi, eps, tol_gi, max_iter, beta=gi_beta,
-                       history=gi_history, mix_tol=mix_tol)
+                       history=gi_history, mix_tol=mix_tol, store_output=gi_store_output)
     psi = gi["psi"] / np.sqrt(np.sum(gi["psi"] ** 2 * w[None, :], axis=1))[:, None]
     eps = gi["eps"]
     mu, f = fermi_level(eps, n_elec, kT)

@@ -563,6 +563,33 @@ def carbon_monoxide_scf(tol_m: float = 3e-7, p: int = 4, half_width: float = 20.
                     e_zz=nuclear_repulsion(mol))
 
 
+def hydrogen_molecule(R: float, tol_m: float = 3e-6, p: int = 4, half_width: float = 20.0,
+                      uniform_levels: int = 3) -> Workload:
+    """H2 with its nuclei at (-R/2, 0, 0) and (R/2, 0, 0) for an SCF run: the
+    adaptive mesh of Section 3.2 (about 170k-200k points at tol_m = 3e-6),
+    one orbital (sigma_g, both electrons) started from the normalised
+    superposition of the atomic 1s orbitals, the hydrogen-atom eigenvalue
+    -0.5 Ha as its guess, and the superposed atomic densities."""
+    mol = Molecule(["H", "H"], np.array([[-0.5 * R, 0.0, 0.0], [0.5 * R, 0.0, 0.0]]))
+    mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
+    pts = mesh.xyz.T
+    s = radial_orbital("1s", 1.0, _dist(pts, mol.pos[0])) + radial_orbital("1s", 1.0, _dist(pts, mol.pos[1]))
+    s = s / np.sqrt(np.sum(s * s * mesh.w))
+    rho = density0(mol, pts)
+    vx = v_ext(mol, pts)
+    veff = vx + v_hartree0(mol, pts) + lda_xc(rho)[1]
+    return Workload(name=f"H2-R{R:.4f}", mesh=mesh, veff=veff, psi=s[None, :], eps=np.array([-0.5]), rho=rho,
+                    vshift=-0.5, theta=0.7, degree=8, leaf_size=2000,
+                    meta={"R": float(R), "tol_m": tol_m, "nuclei": mol.pos.copy()}, vext=vx, n_elec=2.0,
+                    e_zz=nuclear_repulsion(mol))
+
+
+def h2_bond_lengths(seed: int = 5, count: int = 32, lo: float = 1.0, hi: float = 2.0) -> np.ndarray:
+    """Seeded H2 bond lengths for the warm-start data set: `count` values
+    drawn uniformly in [lo, hi] Bohr, sorted."""
+    return np.sort(np.random.default_rng(seed).uniform(lo, hi, size=count))
+
+
 def benzene(seed: int = 3, tol_m: float = 3e-8, p: int = 4, half_width: float = 20.0,
             n_orb: int = 21, uniform_levels: int = 3) -> Workload:
     """C6H6 in the z=0 plane at the paper's geometry (Section 6)."""
@@ -597,6 +624,21 @@ def _molecule_workload(name, mol, mesh, seed, n_orb):
     return Workload(name=name, mesh=mesh, veff=veff, psi=psi, eps=eps, rho=rho, vshift=-0.5,
                     theta=0.7, degree=8, leaf_size=2000, meta={"seed": seed, "n_orb": n_orb}, vext=vx,
                     n_elec=float(sum(ATOM_Z[a] for a in mol.symbols)), e_zz=nuclear_repulsion(mol))
+
+
+def mlp_init(seed: int = 0, n_features: int = 8, hidden: int = 32) -> np.ndarray:
+    """Seeded initial parameters of the warm-start MLP, packed as W1 (H x F),
+    b1 (H), W2 (H x H), b2 (H), W3 (H), b3 (1): weights uniform in
+    +-sqrt(6 / (fan_in + fan_out)) (Glorot and Bengio, 2010), biases zero;
+    float32 values."""
+    rng = np.random.default_rng(seed)
+    F, H = n_features, hidden
+    parts = []
+    for fan_in, fan_out in ((F, H), (H, H), (H, 1)):
+        a = math.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-a, a, size=fan_in * fan_out))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32).astype(np.float64)
 
 
 def random_cube(n: int, seed: int = 0, half_width: float = 1.0):

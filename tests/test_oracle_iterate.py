@@ -137,3 +137,25 @@ def test_converged_orbitals_stay_fixed_and_others_orthogonal():
     np.testing.assert_array_equal(a["eps"][0], b["eps"][0])
     assert abs(np.sum(a["psi"][0] * a["psi"][1] * w)) < 1e-12
     assert abs(a["eps"][0] + 0.5) < 5e-3 and abs(a["eps"][1] + 0.125) < 5e-3
+
+
+def test_store_output_keeps_the_converging_step_output():
+    """With store_output a converged orbital keeps the output of its
+    converging step: the iterate after it0 plain steps, one step past the
+    stored input of Algorithm 2's rule (which the test above pins)."""
+    wl, T, w, r = _h_mesh()
+    p0 = _normalised(np.exp(-r), w)
+    p1 = (2.0 - r) * np.exp(-0.5 * r)
+    p1 = _normalised(p1 - np.sum(p1 * p0 * w) * p0, w)
+    psi0 = np.stack([p0, p1])
+    eps0 = np.array([-0.5, -0.125])
+    kw = dict(tol_gi=3e-4, max_iter=8, mix_tol=0.0)
+    a = oracle.green_iterate(T, 0.7, 6, w, wl.veff, -0.5, psi0, eps0, **kw)
+    c = oracle.green_iterate(T, 0.7, 6, w, wl.veff, -0.5, psi0, eps0, store_output=True, **kw)
+    it0 = c["iters"][0]
+    assert it0 == a["iters"][0] and c["steps"] == a["steps"]
+    b = oracle.green_iterate(T, 0.7, 6, w, wl.veff, -0.5, psi0, eps0, tol_gi=0.0, max_iter=it0, mix_tol=0.0)
+    np.testing.assert_array_equal(c["psi"][0], b["psi"][0])
+    np.testing.assert_array_equal(c["eps"][0], b["eps"][0])
+    assert np.sqrt(np.sum((c["psi"][0] - a["psi"][0]) ** 2 * w)) < 3e-4  # within tol_gi of the input
+    assert abs(np.sum(c["psi"][0] * c["psi"][1] * w)) < 1e-12

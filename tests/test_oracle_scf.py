@@ -42,8 +42,16 @@ def test_fermi_filling_and_degeneracy():
     mu, f = oracle.fermi_level([-1.0, -0.5, -0.5], 4.0, 6.3336e-4)
     np.testing.assert_allclose(f, [1.0, 0.5, 0.5], atol=1e-12)
     assert abs(mu + 0.5) < 1e-12
-    with pytest.raises(ValueError):
-        oracle.fermi_level([-1.0], 2.0, 1e-3)
+    # N_e = 2 N_w fills every state exactly (a closed-shell molecule with
+    # one orbital per electron pair, e.g. H2 with its sigma_g alone)
+    mu, f = oracle.fermi_level([-0.6], 2.0, 6.3336e-4)
+    assert f[0] == 1.0 and mu > -0.6
+    mu, f = oracle.fermi_level([-1.0, -0.4], 4.0, 1e-3)
+    np.testing.assert_allclose(f, 1.0, rtol=0, atol=1e-15)
+    assert abs(2.0 * f.sum() - 4.0) < 1e-15
+    for bad in (2.5, 0.0):
+        with pytest.raises(ValueError):
+            oracle.fermi_level([-1.0], bad, 1e-3)
 
 
 def test_fermi_counts_electrons():
