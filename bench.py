@@ -388,17 +388,20 @@ KT_200K = 200.0 * 3.166811563e-6  # k_B T at 200 K in Ha (Section 6)
 E_REF_LI = -7.334051 - 4.59e-4     # Table timings: E_TAGI(Li) minus its error against the reference
 
 
-def scf_loop(T, wl, xyz, w, params, max_steps=30, tol_scf=1e-4):
+def scf_loop(T, wl, xyz, w, params, max_steps=30, tol_scf=1e-4, store_output=False):
     """SCF iteration (Algorithm 1) from the superposition density to
     ||rho_out - rho_in||_w < tol_scf on one tree: wall-clock seconds per SCF
-    step, Green Iteration steps per SCF step, and the converged energy."""
+    step, Green Iteration steps per SCF step, and the converged energy.
+    store_output: converged orbitals keep their Green step's output rather
+    than its input (Algorithm 2's rule)."""
     import torch
 
     dev = xyz.device
     h = T.tagi_tree_build(xyz, w, params)
-    out = {"tol_scf": tol_scf, "kT_ha": KT_200K, "tol_gi": "3e-3 -> 1e-5 over 4 steps (Section 6)"}
+    out = {"tol_scf": tol_scf, "kT_ha": KT_200K, "tol_gi": "3e-3 -> 1e-5 over 4 steps (Section 6)",
+           "gi_store_output": bool(store_output)}
     try:
-        with T.Scf(h, wl.n_elec, kT=KT_200K, e_zz=wl.e_zz) as scf:
+        with T.Scf(h, wl.n_elec, kT=KT_200K, e_zz=wl.e_zz, gi_store_output=store_output) as scf:
             rho = torch.tensor(wl.rho, device=dev)
             psi = torch.tensor(wl.psi, device=dev)
             vx = torch.tensor(wl.vext, device=dev)
@@ -539,6 +542,7 @@ def main():
     loop = gi_loop(T, wl, xyz, w, params, veff, psi0) if (rank == 0 and not args.no_loop and
                                                           WORKLOAD in ("li", "li-small")) else None
     scf = scf_loop(T, wl, xyz, w, params) if (rank == 0 and not args.no_loop and WORKLOAD == "li") else None
+    scf_so = scf_loop(T, wl, xyz, w, params, store_output=True) if scf is not None else None
     lithium = WORKLOAD in ("li", "li-small")  # the other workloads time Green steps only
 
     # ---- end to end through the public API: pinned host inputs -> device,
@@ -637,6 +641,7 @@ def main():
         "gpu_launches": launches,
         "anterpolation": anterp_line(info, nf, prof, args.steps, clk_mhz, sms),
         "graph_replay": graph,
+        "scf_store_output": scf_so,
         "green_iteration_loop": loop,
         "scf": scf,
         "plain_fp64": plain,

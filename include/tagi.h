@@ -268,7 +268,8 @@ tagi_status tagi_green_graph_destroy(tagi_green_graph* graph);
  * normalisation), giving g(x) = (eps', psi') and the residual
  * r = ||psi' - psi||_w (Algorithm 2 line 7).  Then:
  *   r < tol_gi: the orbital is converged and keeps the input of that step,
- *     (eps^(n), psi^(n)), as Algorithm 2 stores it; it is not convolved again;
+ *     (eps^(n), psi^(n)), as Algorithm 2 stores it -- or, with store_output,
+ *     the step's output g(x) -- and it is not convolved again;
  *   else, before mixing starts: x <- g(x);
  *   else (mixing, which starts once r < mix_tol and stays on): Anderson update
  *     of the last history+1 pairs (x_j, F_j = g(x_j) - x_j): with
@@ -291,6 +292,10 @@ typedef struct {
     double beta;     /* mixing parameter, in (0, 1]; the paper uses 0.5 */
     int history;     /* 0..8 past pairs besides the newest (0: simple mixing) */
     double mix_tol;  /* mixing starts once r < mix_tol (INFINITY: at once; 0: never) */
+    int store_output;/* 0: a converged orbital keeps its step input (Algorithm 2);
+                        1: its step output (inside an SCF iteration the stored
+                        input stops following V_eff once V_eff moves the orbital
+                        by less than tol_gi in one step) */
 } tagi_gi_params;
 typedef struct {
     int steps;            /* Green steps taken */
@@ -326,7 +331,7 @@ tagi_status tagi_green_iterate(tagi_tree* tree, const double* veff, double vshif
  * The tagi_scf object keeps the density-mixing history and the step count;
  * it refers to the tree, which must outlive it. */
 typedef struct {
-    double n_electrons;     /* N_e, 0 < N_e < 2 nw */
+    double n_electrons;     /* N_e, 0 < N_e <= 2 nw (2 nw: every state filled) */
     double kT;              /* k_B T in Ha, > 0 (Section 6: T = 200 K) */
     double e_zz;            /* nuclear repulsion E_ZZ (Eq. electrostatics) */
     double beta;            /* density mixing parameter, in (0, 1] */
@@ -338,6 +343,7 @@ typedef struct {
     double gi_beta;         /* eigenpair mixing parameter, in (0, 1] */
     int gi_history;         /* 0..8 */
     double gi_mix_tol_first;/* >= 0, INFINITY allowed */
+    int gi_store_output;    /* tagi_gi_params.store_output of every Green Iteration */
 } tagi_scf_params;
 typedef struct {
     int step;               /* index of the SCF step just taken (0-based) */
@@ -353,10 +359,67 @@ tagi_status tagi_scf_create(tagi_tree* tree, const tagi_scf_params* params, tagi
  *   eps [host] nw in/out (unshifted); occ [host] nw out or NULL;
  *   rho_out [dev] n out or NULL; report [host] or NULL.
  * Errors: as tagi_green_iterate, and TAGI_ERR_INVALID_ARG for N_e outside
- * (0, 2 nw).  Synchronises the stream. */
+ * (0, 2 nw].  Synchronises the stream. */
 tagi_status tagi_scf_step(tagi_scf* scf, const double* vext, double vshift, double* rho, double* psi, double* eps,
                           int nw, double* occ, double* rho_out, tagi_scf_report* report, void* stream);
 tagi_status tagi_scf_destroy(tagi_scf* scf);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (an addition to the paper's method, whose SCF runs
+ * start from superposed atomic data, Section 6).  A per-point MLP maps the
+ * features of a mesh point to a relative correction y of the normalised
+ * superposition start s: psi = s (1 + y), normalised in the quadrature
+ * norm.  Trained on converged orbitals of this solver's SCF runs; plain
+ * Green Iteration judges its error.
+ *
+ * Model: F = 8 features, two tanh layers of H = 32 units, one output.
+ * Parameters (1377 float64 values, this order): W1 (H x F row-major), b1 (H),
+ * W2 (H x H row-major), b2 (H), W3 (H), b3 (1).  Weights enter the products
+ * rounded to bfloat16 (nearest, ties to even); biases as float32.  The
+ * arithmetic of a point is float32; gradients are summed over points in
+ * float64 in a fixed order (deterministic on a given device); Adam (Kingma
+ * and Ba, 2015) updates float64 master weights.
+ *
+ * Features of a point (float64, then rounded to bfloat16, stored as (n, 8)
+ * uint16 encodings, row-major, 16-byte aligned): with r1 <= r2 the
+ * distances to the two nearest nuclei (lower index first on ties) and R the
+ * distance between those two nuclei,
+ *   [e^-r1, e^-r2, tanh r1, tanh r2, (r2 - r1)/R, tanh((r1 + r2)/R - 1),
+ *    R - 1.5, e^-(r1 + r2 - R)].
+ * ------------------------------------------------------------------------ */
+typedef struct tagi_mlp tagi_mlp;
+typedef struct {
+    double lr;     /* step size, >= 0 */
+    double beta1;  /* in [0, 1) */
+    double beta2;  /* in [0, 1) */
+    double eps;    /* > 0 */
+} tagi_adam_params;
+
+/* params [host] 1377 finite values; n_features must be 8 and hidden 32.
+ * Synchronous (default stream).  Adam's moments start at zero. */
+tagi_status tagi_mlp_create(int n_features, int hidden, const double* params, int64_t n_params, tagi_mlp** out);
+/* Master weights into params [host] (1377 values).  Synchronises stream. */
+tagi_status tagi_mlp_get_params(const tagi_mlp* mlp, double* params, int64_t n_params, void* stream);
+/* xyz [dev] 3*n (structure of arrays); nuclei [host] n_nuclei*3 positions
+ * (2..16, distinct); feat [dev] n*8 uint16 out. */
+tagi_status tagi_mlp_features(const double* xyz, int64_t n, const double* nuclei, int n_nuclei, uint16_t* feat,
+                              void* stream);
+/* y [dev] n float32 out: the network's output for each point. */
+tagi_status tagi_mlp_forward(const tagi_mlp* mlp, const uint16_t* feat, int64_t n, float* y, void* stream);
+/* Loss L = sum_p wt_p (y_p - t_p)^2 and dL/dparams of the current master
+ * weights (the gradient of a rounded weight is applied to its master value):
+ * target, wt [dev] n float32; grad [host] 1377 out; loss [host] out.
+ * Synchronises stream. */
+tagi_status tagi_mlp_gradient(tagi_mlp* mlp, const uint16_t* feat, const float* target, const float* wt, int64_t n,
+                              double* grad, double* loss, void* stream);
+/* One full-batch Adam step on L; loss [host] (L before the step) or NULL
+ * (then nothing synchronises). */
+tagi_status tagi_mlp_train_step(tagi_mlp* mlp, const uint16_t* feat, const float* target, const float* wt,
+                                int64_t n, const tagi_adam_params* adam, double* loss, void* stream);
+/* psi [dev] n out = s (1 + y) / ||s (1 + y)||_w with s, w [dev] n. */
+tagi_status tagi_mlp_warm_start(const tagi_mlp* mlp, const uint16_t* feat, const double* s, const double* w,
+                                int64_t n, double* psi, void* stream);
+tagi_status tagi_mlp_destroy(tagi_mlp* mlp);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* tagi_last_error(void);

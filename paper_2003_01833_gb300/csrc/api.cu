@@ -503,6 +503,7 @@ tagi_status tagi_green_iterate(tagi_tree* tree, const double* veff, double vshif
         TAGI_REQUIRE(gp->beta > 0.0 && gp->beta <= 1.0, "beta must be in (0, 1]");
         TAGI_REQUIRE(gp->history >= 0 && gp->history <= 8, "history must be in [0, 8]");
         TAGI_REQUIRE(gp->mix_tol >= 0.0, "mix_tol must be >= 0 (INFINITY allowed)");
+        TAGI_REQUIRE(gp->store_output == 0 || gp->store_output == 1, "store_output must be 0 or 1");
         for (int o = 0; o < nw; o++) {
             const double es = eps[o] + vshift;
             TAGI_REQUIRE(std::isfinite(es) && es < 0.0, "eps + vshift must be negative (Section 3.3)");
@@ -531,6 +532,7 @@ tagi_status tagi_scf_create(tagi_tree* tree, const tagi_scf_params* p, tagi_scf*
         TAGI_REQUIRE(p->gi_beta > 0.0 && p->gi_beta <= 1.0, "gi_beta must be in (0, 1]");
         TAGI_REQUIRE(p->gi_history >= 0 && p->gi_history <= 8, "gi_history must be in [0, 8]");
         TAGI_REQUIRE(p->gi_mix_tol_first >= 0.0, "gi_mix_tol_first must be >= 0");
+        TAGI_REQUIRE(p->gi_store_output == 0 || p->gi_store_output == 1, "gi_store_output must be 0 or 1");
         *out = reinterpret_cast<tagi_scf*>(new Scf(T, *p));
     });
 }
@@ -544,7 +546,7 @@ tagi_status tagi_scf_step(tagi_scf* scf, const double* vext, double vshift, doub
         TAGI_REQUIRE(vext != nullptr && rho != nullptr && psi != nullptr && eps != nullptr,
                      "vext, rho, psi or eps is NULL");
         TAGI_REQUIRE(nw >= 1 && nw <= kMaxCallFields, "nw must be in [1, 128]");
-        TAGI_REQUIRE(S->p.n_electrons < 2.0 * nw, "n_electrons must be below 2 nw");
+        TAGI_REQUIRE(S->p.n_electrons <= 2.0 * nw, "n_electrons must not exceed 2 nw");
         TAGI_REQUIRE(std::isfinite(vshift), "vshift must be finite");
         for (int o = 0; o < nw; o++) {
             const double es = eps[o] + vshift;

@@ -350,6 +350,13 @@ void green_iterate(Tree& T, const double* veff, double vshift, double* psi, doub
             if (r < gp.tol_gi) {
                 conv[o] = 1;
                 iters[o] = step + 1;
+                if (gp.store_output) {
+                    TAGI_CUDA(cudaMemcpyAsync(psi + (size_t)o * n, U + (size_t)a * n, sizeof(double) * n,
+                                              cudaMemcpyDeviceToDevice, s));
+                    launch(k_copy_scalar, 1, 1, 0, s, eps_all.as<double>() + o,
+                           (const double*)(eps_new.as<double>() + a));
+                    TAGI_LAUNCH_CHECK();
+                }
                 continue;
             }
             if (r < gp.mix_tol) mixing[o] = 1;
@@ -462,7 +469,7 @@ void scf_step(Scf& S, const double* vext, double vshift, double* rho, double* ps
     else if (k < S.p.tol_gi_ramp)
         tol = S.p.tol_gi_first * std::pow(S.p.tol_gi_final / S.p.tol_gi_first, (double)k / S.p.tol_gi_ramp);
     tagi_gi_params gp{tol, S.p.gi_max_iter, S.p.gi_beta, S.p.gi_history,
-                      k == 0 ? S.p.gi_mix_tol_first : (double)INFINITY};
+                      k == 0 ? S.p.gi_mix_tol_first : (double)INFINITY, S.p.gi_store_output};
     tagi_gi_stats gst{};
     green_iterate(T, veff.as<double>(), vshift, psi, eps, nw, gp, nullptr, nullptr, &gst);
     for (int o = 0; o < nw; o++) orthonormalize(T, psi + (size_t)o * n, {}, sc + 8);

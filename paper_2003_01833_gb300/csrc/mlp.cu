@@ -1,0 +1,561 @@
+// Learned warm start for SCF runs of molecules: point features, a per-point
+// MLP (F = 8 inputs, two tanh layers of H = 32, one output), its gradient and
+// Adam.  Weights enter the products rounded to bfloat16 and features are
+// stored as bfloat16; the arithmetic of a point is float32, gradients are
+// accumulated over points in float64 in a fixed order (deterministic for a
+// given device), and Adam keeps float64 master weights.
+//
+// Not a method of the paper: its SCF runs start from superposed atomic data
+// (Section 6).  The model predicts a relative correction y of the normalised
+// superposition start s, psi = s (1 + y).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "tagi_internal.cuh"
+
+namespace tagi {
+namespace {
+
+constexpr int kF = 8;
+constexpr int kH = 32;
+constexpr int oW1 = 0, oB1 = kH * kF, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH, oB3 = oW3 + kH;
+constexpr int kP = oB3 + 1;  // 1377 parameters
+constexpr int kPPad = 1380;  // float slots of the weights in shared memory (keeps the stash 16-byte aligned)
+constexpr int kThreads = 128;
+// Stash row of one point for the gradient reduction: x | h1 | h2 | dz1 | dz2 |
+// dy | 1.  An odd stride keeps the rows of a warp's 32 points in 32 banks.
+constexpr int cX = 0, cH1 = 8, cH2 = 40, cD1 = 72, cD2 = 104, cDy = 136, cOne = 137, kStride = 139;
+constexpr int kEntries = (kP + kThreads - 1) / kThreads;  // gradient entries per thread
+constexpr int kMaxNuclei = 16;
+constexpr size_t kGradSmem = sizeof(float) * (kPPad + (size_t)kThreads * kStride);
+
+struct Nuclei {
+    double x[kMaxNuclei], y[kMaxNuclei], z[kMaxNuclei];
+    int m;
+};
+
+// Nearest bfloat16 value of x, ties to even, from the float64 value: x / q
+// with q the spacing of bfloat16 values at x (a power of two, so exact),
+// rounded to an integer half-to-even, scaled back.  The result has 8
+// significant bits within float32's exponent range, so the float32
+// conversion is exact and its high half is the bfloat16 encoding.
+__device__ __forceinline__ uint16_t bf16_bits(double x)
+{
+    if (isnan(x)) return 0x7FC0;
+    if (x == 0.0) return signbit(x) ? 0x8000 : 0;
+    int e;
+    frexp(x, &e);
+    const double q = ldexp(1.0, max(e - 8, -133));
+    const double r = rint(x / q) * q;
+    return (uint16_t)(__float_as_uint((float)r) >> 16);
+}
+
+__device__ __forceinline__ float bf16_float(uint32_t b) { return __uint_as_float(b << 16); }
+
+__device__ __forceinline__ bool is_weight(int e)
+{
+    return (e >= oW1 && e < oB1) || (e >= oW2 && e < oB2) || (e >= oW3 && e < oB3);
+}
+
+// Weights rounded to bfloat16, biases as float32, into shared memory.
+__device__ __forceinline__ void load_params(float* sw, const double* __restrict__ master)
+{
+    for (int e = threadIdx.x; e < kP; e += blockDim.x)
+        sw[e] = is_weight(e) ? bf16_float(bf16_bits(master[e])) : (float)master[e];
+}
+
+__device__ __forceinline__ void load_x(const uint16_t* __restrict__ feat, int64_t i, float x[kF])
+{
+    const uint4 v = *reinterpret_cast<const uint4*>(feat + i * kF);
+    const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        x[2 * k] = bf16_float(u[k] & 0xFFFFu);
+        x[2 * k + 1] = bf16_float(u[k] >> 16);
+    }
+}
+
+__device__ __forceinline__ void layer1(const float* sw, const float x[kF], float h1[kH])
+{
+#pragma unroll
+    for (int i = 0; i < kH; i++) {
+        float z = sw[oB1 + i];
+#pragma unroll
+        for (int f = 0; f < kF; f++) z = fmaf(sw[oW1 + i * kF + f], x[f], z);
+        h1[i] = tanhf(z);
+    }
+}
+
+__device__ __forceinline__ float layer2_unit(const float* sw, const float h1[kH], int j)
+{
+    float z = sw[oB2 + j];
+#pragma unroll
+    for (int i = 0; i < kH; i++) z = fmaf(sw[oW2 + j * kH + i], h1[i], z);
+    return tanhf(z);
+}
+
+// ------------------------------------------------------------------ kernels
+// Features of a point (float64, rounded once to bfloat16): with r1 <= r2 the
+// distances to the two nearest nuclei (the lower index first on ties) and R
+// their separation, [e^-r1, e^-r2, tanh r1, tanh r2, (r2 - r1)/R,
+// tanh((r1 + r2)/R - 1), R - 1.5, e^-(r1 + r2 - R)].  Sums of squares are
+// formed left to right without contraction.
+__global__ void k_features(const double* __restrict__ xyz, int64_t n, Nuclei nuc, uint16_t* __restrict__ feat)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double px = xyz[i], py = xyz[n + i], pz = xyz[2 * n + i];
+    double d1 = INFINITY, d2 = INFINITY;
+    int a1 = 0, a2 = 1;
+    for (int a = 0; a < nuc.m; a++) {
+        const double dx = px - nuc.x[a], dy = py - nuc.y[a], dz = pz - nuc.z[a];
+        const double d = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+        if (d < d1) {
+            d2 = d1;
+            a2 = a1;
+            d1 = d;
+            a1 = a;
+        } else if (d < d2) {
+            d2 = d;
+            a2 = a;
+        }
+    }
+    const double ex = nuc.x[a1] - nuc.x[a2], ey = nuc.y[a1] - nuc.y[a2], ez = nuc.z[a1] - nuc.z[a2];
+    const double R = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+    const double s12 = __dadd_rn(d1, d2);
+    const double f[kF] = {exp(-d1),
+                          exp(-d2),
+                          tanh(d1),
+                          tanh(d2),
+                          __dsub_rn(d2, d1) / R,
+                          tanh(__dsub_rn(s12 / R, 1.0)),
+                          __dsub_rn(R, 1.5),
+                          exp(-__dsub_rn(s12, R))};
+    uint32_t u[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) u[k] = (uint32_t)bf16_bits(f[2 * k]) | ((uint32_t)bf16_bits(f[2 * k + 1]) << 16);
+    *reinterpret_cast<uint4*>(feat + i * kF) = make_uint4(u[0], u[1], u[2], u[3]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_mlp_forward(const uint16_t* __restrict__ feat, int64_t n,
+                                                          const double* __restrict__ master, float* __restrict__ y)
+{
+    __shared__ float sw[kPPad];
+    load_params(sw, master);
+    __syncthreads();
+#pragma unroll 1
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        // the weights are read from shared memory in every iteration rather
+        // than all 1377 held in registers across the loop
+        asm volatile("" ::: "memory");
+        float x[kF], h1[kH];
+        load_x(feat, i, x);
+        layer1(sw, x, h1);
+        float out = sw[oB3];
+#pragma unroll 1
+        for (int j = 0; j < kH; j++) out = fmaf(sw[oW3 + j], layer2_unit(sw, h1, j), out);
+        y[i] = out;
+    }
+}
+
+// Loss L = sum_p wt_p (y_p - t_p)^2 and its gradient: each thread runs the
+// forward and backward pass of one point of a 128-point tile and stashes
+// (x, h1, h2, dz1, dz2, dy) in shared memory; then each thread forms its own
+// gradient entries (outer-product sums over the tile in point order, float32)
+// and adds them to float64 accumulators.  Tiles are strided over a fixed
+// grid; per-block partials [grid][kP + 1] (the loss last) are reduced by
+// k_mlp_adam in block order.
+__global__ void __launch_bounds__(kThreads) k_mlp_grad(const uint16_t* __restrict__ feat,
+                                                       const float* __restrict__ target, const float* __restrict__ wt,
+                                                       int64_t n, const double* __restrict__ master,
+                                                       double* __restrict__ partial)
+{
+    extern __shared__ float sm[];
+    float* sw = sm;
+    float* st = sm + kPPad;
+    __shared__ double sl[kThreads];
+    const int tid = threadIdx.x;
+    load_params(sw, master);
+
+    int ca[kEntries], cb[kEntries];
+    double acc[kEntries];
+#pragma unroll
+    for (int k = 0; k < kEntries; k++) {
+        const int e = tid + k * kThreads;
+        int a = cDy, b = cOne;  // entries past kP: computed, never written
+        if (e < oB1) {
+            a = cD1 + e / kF;
+            b = cX + e % kF;
+        } else if (e < oW2) {
+            a = cD1 + (e - oB1);
+            b = cOne;
+        } else if (e < oB2) {
+            a = cD2 + (e - oW2) / kH;
+            b = cH1 + (e - oW2) % kH;
+        } else if (e < oW3) {
+            a = cD2 + (e - oB2);
+            b = cOne;
+        } else if (e < oB3) {
+            a = cDy;
+            b = cH2 + (e - oW3);
+        }
+        ca[k] = a;
+        cb[k] = b;
+        acc[k] = 0.0;
+    }
+    double lsum = 0.0;
+    __syncthreads();
+
+    const int64_t ntiles = (n + kThreads - 1) / kThreads;
+    float* row = st + tid * kStride;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t i = tile * kThreads + tid;
+        if (i < n) {
+            float x[kF], h1[kH];
+            load_x(feat, i, x);
+            layer1(sw, x, h1);
+            float y = sw[oB3];
+            for (int j = 0; j < kH; j++) {
+                const float a = layer2_unit(sw, h1, j);
+                row[cH2 + j] = a;
+                y = fmaf(sw[oW3 + j], a, y);
+            }
+            const float r = y - target[i];
+            const float dy = 2.0f * wt[i] * r;
+            lsum += (double)wt[i] * (double)r * (double)r;
+            float g1[kH];
+#pragma unroll
+            for (int q = 0; q < kH; q++) g1[q] = 0.0f;
+            for (int j = 0; j < kH; j++) {
+                const float a = row[cH2 + j];
+                const float d2 = dy * sw[oW3 + j] * (1.0f - a * a);
+                row[cD2 + j] = d2;
+#pragma unroll
+                for (int q = 0; q < kH; q++) g1[q] = fmaf(sw[oW2 + j * kH + q], d2, g1[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < kH; q++) {
+                row[cH1 + q] = h1[q];
+                row[cD1 + q] = g1[q] * (1.0f - h1[q] * h1[q]);
+            }
+#pragma unroll
+            for (int f = 0; f < kF; f++) row[cX + f] = x[f];
+            row[cDy] = dy;
+            row[cOne] = 1.0f;
+        } else {
+            for (int c = 0; c < kStride; c++) row[c] = 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kEntries; k++) {
+            float s = 0.0f;
+            for (int p = 0; p < kThreads; p++) s = fmaf(st[p * kStride + ca[k]], st[p * kStride + cb[k]], s);
+            acc[k] += (double)s;
+        }
+        __syncthreads();
+    }
+    double* out = partial + (size_t)blockIdx.x * (kP + 1);
+#pragma unroll
+    for (int k = 0; k < kEntries; k++) {
+        const int e = tid + k * kThreads;
+        if (e < kP) out[e] = acc[k];
+    }
+    sl[tid] = lsum;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int t = 0; t < kThreads; t++) s += sl[t];
+        out[kP] = s;
+    }
+}
+
+// Gradient and loss from the per-block partials (block order), then, if
+// apply, one Adam step on the float64 master weights (c1 = 1 - beta1^t,
+// c2 = 1 - beta2^t).
+__global__ void k_mlp_adam(const double* __restrict__ partial, int nblk, double* __restrict__ master,
+                           double* __restrict__ m, double* __restrict__ v, double lr, double beta1, double beta2,
+                           double eps, double c1, double c2, int apply, double* __restrict__ grad_out,
+                           double* __restrict__ loss_out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > kP) return;
+    double g = 0.0;
+    for (int b = 0; b < nblk; b++) g += partial[(size_t)b * (kP + 1) + e];
+    if (e == kP) {
+        *loss_out = g;
+        return;
+    }
+    grad_out[e] = g;
+    if (!apply) return;
+    const double mm = beta1 * m[e] + (1.0 - beta1) * g;
+    const double vv = beta2 * v[e] + (1.0 - beta2) * g * g;
+    m[e] = mm;
+    v[e] = vv;
+    master[e] -= (lr * (mm / c1)) / (sqrt(vv / c2) + eps);
+}
+
+// psi = s (1 + y) and per-block partial sums of psi^2 w (block order).
+__global__ void __launch_bounds__(256) k_warm_apply(const float* __restrict__ y, const double* __restrict__ s,
+                                                    const double* __restrict__ w, int64_t n,
+                                                    double* __restrict__ psi, double* __restrict__ part)
+{
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+        const double p = s[i] * (1.0 + (double)y[i]);
+        psi[i] = p;
+        acc += p * p * w[i];
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_warm_scale(double* __restrict__ psi, int64_t n, const double* __restrict__ part, int nblk)
+{
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += part[b];
+    const double inv = 1.0 / sqrt(s);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        psi[i] *= inv;
+}
+
+// ------------------------------------------------------------------ object
+struct Mlp {
+    int dev = 0;
+    int sms = 0;
+    int64_t step = 0;
+    DevBuf master, m, v, partial, grad, loss, part;
+    std::string err;
+};
+
+int grad_grid(const Mlp& M, int64_t n)
+{
+    const int64_t tiles = (n + kThreads - 1) / kThreads;
+    return (int)std::min<int64_t>(tiles, 2LL * M.sms);
+}
+
+thread_local std::string g_mlp_err;
+
+template <class F>
+tagi_status guarded_mlp(F&& f)
+{
+    try {
+        report_error(TAGI_OK, "");
+        f();
+        return TAGI_OK;
+    } catch (const Error& e) {
+        g_mlp_err = e.what();
+        return report_error(e.status, g_mlp_err.c_str());
+    } catch (const std::bad_alloc&) {
+        return report_error(TAGI_ERR_OOM, "host allocation failed");
+    } catch (const std::exception& e) {
+        g_mlp_err = e.what();
+        return report_error(TAGI_ERR_CUDA, g_mlp_err.c_str());
+    }
+}
+
+Mlp* as_mlp(const tagi_mlp* p)
+{
+    TAGI_REQUIRE(p != nullptr, "mlp is NULL");
+    return reinterpret_cast<Mlp*>(const_cast<tagi_mlp*>(p));
+}
+
+void check_data(const void* feat, int64_t n)
+{
+    TAGI_REQUIRE(feat != nullptr, "feat is NULL");
+    TAGI_REQUIRE(n >= 1, "n must be >= 1");
+    TAGI_REQUIRE(((uintptr_t)feat & 15) == 0, "feat must be 16-byte aligned");
+}
+
+// Gradient (and loss) of the current master weights into M.grad / M.loss;
+// with apply, one Adam step as well.
+void grad_pass(Mlp& M, const uint16_t* feat, const float* target, const float* wt, int64_t n,
+               const tagi_adam_params* a, bool apply, cudaStream_t s)
+{
+    const int grid = grad_grid(M, n);
+    M.partial.ensure(sizeof(double) * (size_t)grid * (kP + 1));
+    launch(k_mlp_grad, grid, kThreads, kGradSmem, s, feat, target, wt, n, M.master.as<double>(),
+           M.partial.as<double>());
+    double c1 = 1.0, c2 = 1.0, lr = 0.0, b1 = 0.9, b2 = 0.999, eps = 1e-8;
+    if (apply) {
+        M.step += 1;
+        lr = a->lr;
+        b1 = a->beta1;
+        b2 = a->beta2;
+        eps = a->eps;
+        c1 = 1.0 - std::pow(b1, (double)M.step);
+        c2 = 1.0 - std::pow(b2, (double)M.step);
+    }
+    launch(k_mlp_adam, (kP + 1 + 127) / 128, 128, 0, s, M.partial.as<double>(), grid, M.master.as<double>(),
+           M.m.as<double>(), M.v.as<double>(), lr, b1, b2, eps, c1, c2, apply ? 1 : 0, M.grad.as<double>(),
+           M.loss.as<double>());
+    TAGI_LAUNCH_CHECK();
+}
+
+}  // namespace
+}  // namespace tagi
+
+using namespace tagi;
+
+extern "C" {
+
+tagi_status tagi_mlp_create(int n_features, int hidden, const double* params, int64_t n_params, tagi_mlp** out)
+{
+    return guarded_mlp([&] {
+        TAGI_REQUIRE(out != nullptr, "out is NULL");
+        *out = nullptr;
+        TAGI_REQUIRE(n_features == kF && hidden == kH, "the model has 8 features and 32 hidden units");
+        TAGI_REQUIRE(params != nullptr && n_params == kP, "params must hold 1377 values");
+        for (int64_t e = 0; e < n_params; e++) TAGI_REQUIRE(std::isfinite(params[e]), "params must be finite");
+        TAGI_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem));
+        auto* M = new Mlp();
+        try {
+            TAGI_CUDA(cudaGetDevice(&M->dev));
+            TAGI_CUDA(cudaDeviceGetAttribute(&M->sms, cudaDevAttrMultiProcessorCount, M->dev));
+            AllocStream as(nullptr);
+            M->master.ensure(sizeof(double) * kP);
+            M->m.ensure(sizeof(double) * kP);
+            M->v.ensure(sizeof(double) * kP);
+            M->grad.ensure(sizeof(double) * kP);
+            M->loss.ensure(sizeof(double));
+            TAGI_CUDA(cudaMemcpy(M->master.p, params, sizeof(double) * kP, cudaMemcpyHostToDevice));
+            TAGI_CUDA(cudaMemset(M->m.p, 0, sizeof(double) * kP));
+            TAGI_CUDA(cudaMemset(M->v.p, 0, sizeof(double) * kP));
+        } catch (...) {
+            delete M;
+            throw;
+        }
+        *out = reinterpret_cast<tagi_mlp*>(M);
+    });
+}
+
+tagi_status tagi_mlp_get_params(const tagi_mlp* mlp, double* params, int64_t n_params, void* stream)
+{
+    return guarded_mlp([&] {
+        Mlp* M = as_mlp(mlp);
+        TAGI_REQUIRE(params != nullptr && n_params == kP, "params must hold 1377 values");
+        cudaStream_t s = (cudaStream_t)stream;
+        TAGI_CUDA(cudaMemcpyAsync(params, M->master.p, sizeof(double) * kP, cudaMemcpyDeviceToHost, s));
+        TAGI_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+tagi_status tagi_mlp_features(const double* xyz, int64_t n, const double* nuclei, int n_nuclei, uint16_t* feat,
+                              void* stream)
+{
+    return guarded_mlp([&] {
+        TAGI_REQUIRE(xyz != nullptr && nuclei != nullptr, "xyz or nuclei is NULL");
+        check_data(feat, n);
+        TAGI_REQUIRE(n_nuclei >= 2 && n_nuclei <= kMaxNuclei, "need 2 to 16 nuclei");
+        Nuclei nu{};
+        nu.m = n_nuclei;
+        for (int a = 0; a < n_nuclei; a++) {
+            nu.x[a] = nuclei[3 * a];
+            nu.y[a] = nuclei[3 * a + 1];
+            nu.z[a] = nuclei[3 * a + 2];
+            TAGI_REQUIRE(std::isfinite(nu.x[a]) && std::isfinite(nu.y[a]) && std::isfinite(nu.z[a]),
+                         "nuclei must be finite");
+        }
+        for (int a = 0; a < n_nuclei; a++)
+            for (int b = 0; b < a; b++)
+                TAGI_REQUIRE(nu.x[a] != nu.x[b] || nu.y[a] != nu.y[b] || nu.z[a] != nu.z[b],
+                             "nuclei must be distinct");
+        launch(k_features, (unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream, xyz, n, nu, feat);
+        TAGI_LAUNCH_CHECK();
+    });
+}
+
+tagi_status tagi_mlp_forward(const tagi_mlp* mlp, const uint16_t* feat, int64_t n, float* y, void* stream)
+{
+    return guarded_mlp([&] {
+        Mlp* M = as_mlp(mlp);
+        check_data(feat, n);
+        TAGI_REQUIRE(y != nullptr, "y is NULL");
+        const int64_t blocks = std::min<int64_t>((n + kThreads - 1) / kThreads, 8LL * M->sms);
+        launch(k_mlp_forward, (unsigned)blocks, kThreads, 0, (cudaStream_t)stream, feat, n, M->master.as<double>(),
+               y);
+        TAGI_LAUNCH_CHECK();
+    });
+}
+
+tagi_status tagi_mlp_gradient(tagi_mlp* mlp, const uint16_t* feat, const float* target, const float* wt, int64_t n,
+                              double* grad, double* loss, void* stream)
+{
+    return guarded_mlp([&] {
+        Mlp* M = as_mlp(mlp);
+        check_data(feat, n);
+        TAGI_REQUIRE(target != nullptr && wt != nullptr, "target or wt is NULL");
+        TAGI_REQUIRE(grad != nullptr && loss != nullptr, "grad or loss is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        AllocStream as(s);
+        grad_pass(*M, feat, target, wt, n, nullptr, false, s);
+        TAGI_CUDA(cudaMemcpyAsync(grad, M->grad.p, sizeof(double) * kP, cudaMemcpyDeviceToHost, s));
+        TAGI_CUDA(cudaMemcpyAsync(loss, M->loss.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        TAGI_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+tagi_status tagi_mlp_train_step(tagi_mlp* mlp, const uint16_t* feat, const float* target, const float* wt,
+                                int64_t n, const tagi_adam_params* adam, double* loss, void* stream)
+{
+    return guarded_mlp([&] {
+        Mlp* M = as_mlp(mlp);
+        check_data(feat, n);
+        TAGI_REQUIRE(target != nullptr && wt != nullptr && adam != nullptr, "target, wt or adam is NULL");
+        TAGI_REQUIRE(std::isfinite(adam->lr) && adam->lr >= 0.0, "lr must be >= 0");
+        TAGI_REQUIRE(adam->beta1 >= 0.0 && adam->beta1 < 1.0 && adam->beta2 >= 0.0 && adam->beta2 < 1.0,
+                     "beta1 and beta2 must be in [0, 1)");
+        TAGI_REQUIRE(adam->eps > 0.0, "eps must be > 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        AllocStream as(s);
+        grad_pass(*M, feat, target, wt, n, adam, true, s);
+        if (loss) {
+            TAGI_CUDA(cudaMemcpyAsync(loss, M->loss.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+            TAGI_CUDA(cudaStreamSynchronize(s));
+        }
+    });
+}
+
+tagi_status tagi_mlp_warm_start(const tagi_mlp* mlp, const uint16_t* feat, const double* s0, const double* w,
+                                int64_t n, double* psi, void* stream)
+{
+    return guarded_mlp([&] {
+        Mlp* M = as_mlp(mlp);
+        check_data(feat, n);
+        TAGI_REQUIRE(s0 != nullptr && w != nullptr && psi != nullptr, "s, w or psi is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        AllocStream as(s);
+        DevBuf y;
+        y.ensure(sizeof(float) * (size_t)n);
+        const int64_t fb = std::min<int64_t>((n + kThreads - 1) / kThreads, 8LL * M->sms);
+        launch(k_mlp_forward, (unsigned)fb, kThreads, 0, s, feat, n, M->master.as<double>(), y.as<float>());
+        const int nb = (int)std::min<int64_t>((n + 255) / 256, 4LL * M->sms);
+        M->part.ensure(sizeof(double) * nb);
+        launch(k_warm_apply, nb, 256, 0, s, (const float*)y.as<float>(), s0, w, n, psi, M->part.as<double>());
+        launch(k_warm_scale, (unsigned)std::min<int64_t>((n + 255) / 256, 8LL * M->sms), 256, 0, s, psi, n,
+               (const double*)M->part.as<double>(), nb);
+        TAGI_LAUNCH_CHECK();
+    });
+}
+
+tagi_status tagi_mlp_destroy(tagi_mlp* mlp)
+{
+    return guarded_mlp([&] {
+        if (!mlp) return;
+        Mlp* M = reinterpret_cast<Mlp*>(mlp);
+        TAGI_CUDA(cudaDeviceSynchronize());
+        delete M;
+    });
+}
+
+}  // extern "C"

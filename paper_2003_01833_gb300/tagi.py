@@ -53,7 +53,7 @@ class tagi_tree_stats(ctypes.Structure):
 
 class tagi_gi_params(ctypes.Structure):
     _fields_ = [("tol_gi", ctypes.c_double), ("max_iter", ctypes.c_int), ("beta", ctypes.c_double),
-                ("history", ctypes.c_int), ("mix_tol", ctypes.c_double)]
+                ("history", ctypes.c_int), ("mix_tol", ctypes.c_double), ("store_output", ctypes.c_int)]
 
 
 class tagi_gi_stats(ctypes.Structure):
@@ -64,7 +64,8 @@ class tagi_scf_params(ctypes.Structure):
     _fields_ = [("n_electrons", ctypes.c_double), ("kT", ctypes.c_double), ("e_zz", ctypes.c_double),
                 ("beta", ctypes.c_double), ("history", ctypes.c_int), ("tol_gi_first", ctypes.c_double),
                 ("tol_gi_final", ctypes.c_double), ("tol_gi_ramp", ctypes.c_int), ("gi_max_iter", ctypes.c_int),
-                ("gi_beta", ctypes.c_double), ("gi_history", ctypes.c_int), ("gi_mix_tol_first", ctypes.c_double)]
+                ("gi_beta", ctypes.c_double), ("gi_history", ctypes.c_int), ("gi_mix_tol_first", ctypes.c_double),
+                ("gi_store_output", ctypes.c_int)]
 
 
 class tagi_scf_report(ctypes.Structure):
@@ -79,6 +80,11 @@ _vp = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
 _I32 = ctypes.POINTER(ctypes.c_int32)
 _I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+class tagi_adam_params(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
 
 
 def lib():
@@ -120,6 +126,18 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.tagi_yukawa_direct_noalloc.argtypes = [_vp, _vp, _vp, _D, ctypes.c_int, ctypes.c_int64, _vp, _vp]
         L.tagi_yukawa_direct_noalloc.restype = ctypes.c_int
+        L.tagi_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_int64, ctypes.POINTER(_vp)]
+        L.tagi_mlp_get_params.argtypes = [_vp, _D, ctypes.c_int64, _vp]
+        L.tagi_mlp_features.argtypes = [_vp, ctypes.c_int64, _D, ctypes.c_int, _vp, _vp]
+        L.tagi_mlp_forward.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+        L.tagi_mlp_gradient.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _D, _D, _vp]
+        L.tagi_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(tagi_adam_params),
+                                          _D, _vp]
+        L.tagi_mlp_warm_start.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp]
+        L.tagi_mlp_destroy.argtypes = [_vp]
+        for name in ("tagi_mlp_create", "tagi_mlp_get_params", "tagi_mlp_features", "tagi_mlp_forward",
+                     "tagi_mlp_gradient", "tagi_mlp_train_step", "tagi_mlp_warm_start", "tagi_mlp_destroy"):
+            getattr(L, name).restype = ctypes.c_int
         L.tagi_profile_read.argtypes = [ctypes.c_int, _D, _I64]
         L.tagi_last_error.restype = ctypes.c_char_p
         L.tagi_version.restype = ctypes.c_char_p
@@ -296,7 +314,7 @@ def tagi_green_step(tree, veff, vshift, psi, eps, rho=None, vh=None, stream=None
 
 
 def tagi_green_iterate(tree, veff, vshift, psi, eps, tol_gi, max_iter, beta=0.5, history=5, mix_tol=math.inf,
-                       stream=None):
+                       stream=None, store_output=False):
     """Green Iteration with Anderson mixing of eigenpairs until every orbital's
     residual is below tol_gi (or max_iter steps).  psi: (nw, n) float64 CUDA,
     updated in place; eps: nw host floats.
@@ -312,7 +330,8 @@ def tagi_green_iterate(tree, veff, vshift, psi, eps, tol_gi, max_iter, beta=0.5,
         raise ValueError("one eigenvalue per orbital")
     res = np.full(nw, np.nan)
     its = np.full(nw, -1, dtype=np.int32)
-    gp = tagi_gi_params(float(tol_gi), int(max_iter), float(beta), int(history), float(mix_tol))
+    gp = tagi_gi_params(float(tol_gi), int(max_iter), float(beta), int(history), float(mix_tol),
+                        int(bool(store_output)))
     st = tagi_gi_stats()
     _check(lib().tagi_green_iterate(tree, _dptr(veff, "veff"), float(vshift), _dptr(psi, "psi"), ep, nw,
                                     ctypes.byref(gp), res.ctypes.data_as(_D), its.ctypes.data_as(_I32),
@@ -327,11 +346,11 @@ class Scf:
 
     def __init__(self, tree, n_electrons, kT=6.3336e-4, e_zz=0.0, beta=0.5, history=5, tol_gi_first=3e-3,
                  tol_gi_final=1e-5, tol_gi_ramp=4, gi_max_iter=100, gi_beta=0.5, gi_history=5,
-                 gi_mix_tol_first=math.inf):
+                 gi_mix_tol_first=math.inf, gi_store_output=False):
         self.tree = tree
         p = tagi_scf_params(float(n_electrons), float(kT), float(e_zz), float(beta), int(history),
                             float(tol_gi_first), float(tol_gi_final), int(tol_gi_ramp), int(gi_max_iter),
-                            float(gi_beta), int(gi_history), float(gi_mix_tol_first))
+                            float(gi_beta), int(gi_history), float(gi_mix_tol_first), int(bool(gi_store_output)))
         h = _vp()
         _check(lib().tagi_scf_create(tree, ctypes.byref(p), ctypes.byref(h)))
         self.handle = h
@@ -477,3 +496,112 @@ class Tree:
 
     def info(self):
         return tagi_tree_info(self.handle)
+
+
+# ------------------------------------------------------------ learned warm start
+MLP_FEATURES = 8
+MLP_HIDDEN = 32
+MLP_PARAMS = 1377
+
+
+def _tptr(t, name, dtype, numel):
+    """Device pointer of a contiguous CUDA tensor of the given dtype."""
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def tagi_mlp_features(xyz, nuclei, feat=None, stream=None):
+    """xyz (3, n) float64 CUDA; nuclei (m, 3) host positions.  Returns the
+    (n, 8) bfloat16 encodings as an int16 CUDA tensor (feat if given)."""
+    import torch
+
+    n = xyz.numel() // 3
+    nu = np.ascontiguousarray(np.asarray(nuclei, dtype=np.float64).reshape(-1, 3))
+    if feat is None:
+        feat = torch.empty((n, MLP_FEATURES), dtype=torch.int16, device=xyz.device)
+    _check(lib().tagi_mlp_features(_dptr(xyz, "xyz", 3 * n), n, nu.ctypes.data_as(_D), nu.shape[0],
+                                   _tptr(feat, "feat", torch.int16, n * MLP_FEATURES), _stream(stream)))
+    return feat
+
+
+class Mlp:
+    """Warm-start MLP on the device (tagi_mlp_*).  Use as a context manager
+    or call close()."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        h = _vp()
+        _check(lib().tagi_mlp_create(MLP_FEATURES, MLP_HIDDEN, p.ctypes.data_as(_D), p.size, ctypes.byref(h)))
+        self.handle = h
+
+    def params(self, stream=None):
+        out = np.empty(MLP_PARAMS)
+        _check(lib().tagi_mlp_get_params(self.handle, out.ctypes.data_as(_D), MLP_PARAMS, _stream(stream)))
+        return out
+
+    def _data(self, feat, target=None, wt=None):
+        import torch
+
+        n = feat.shape[0]
+        args = [_tptr(feat, "feat", torch.int16, n * MLP_FEATURES)]
+        if target is not None:
+            args += [_tptr(target, "target", torch.float32, n), _tptr(wt, "wt", torch.float32, n)]
+        return n, args
+
+    def forward(self, feat, y=None, stream=None):
+        import torch
+
+        n, (fp,) = self._data(feat)
+        if y is None:
+            y = torch.empty(n, dtype=torch.float32, device=feat.device)
+        _check(lib().tagi_mlp_forward(self.handle, fp, n, _tptr(y, "y", torch.float32, n), _stream(stream)))
+        return y
+
+    def gradient(self, feat, target, wt, stream=None):
+        """(loss, gradient) of the current master weights."""
+        n, (fp, tp, wp) = self._data(feat, target, wt)
+        g = np.empty(MLP_PARAMS)
+        loss = np.zeros(1)
+        _check(lib().tagi_mlp_gradient(self.handle, fp, tp, wp, n, g.ctypes.data_as(_D), loss.ctypes.data_as(_D),
+                                       _stream(stream)))
+        return float(loss[0]), g
+
+    def train_step(self, feat, target, wt, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=False, stream=None):
+        n, (fp, tp, wp) = self._data(feat, target, wt)
+        a = tagi_adam_params(float(lr), float(beta1), float(beta2), float(eps))
+        loss = np.zeros(1)
+        _check(lib().tagi_mlp_train_step(self.handle, fp, tp, wp, n, ctypes.byref(a),
+                                         loss.ctypes.data_as(_D) if want_loss else None, _stream(stream)))
+        return float(loss[0]) if want_loss else None
+
+    def warm_start(self, feat, s, w, psi=None, stream=None):
+        import torch
+
+        n, (fp,) = self._data(feat)
+        if psi is None:
+            psi = torch.empty(n, dtype=torch.float64, device=feat.device)
+        _check(lib().tagi_mlp_warm_start(self.handle, fp, _dptr(s, "s", n), _dptr(w, "w", n), n,
+                                         _dptr(psi, "psi", n), _stream(stream)))
+        return psi
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tagi_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

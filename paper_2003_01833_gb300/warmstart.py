@@ -1,0 +1,277 @@
+"""Learned warm start for SCF runs of molecules: a small per-point MLP that
+predicts the converged orbital from features of the geometry (distances to
+the nuclei and the superposed atomic Slater orbitals), and a second one that
+predicts the eigenvalue from the bond length.  Both are trained on converged
+orbitals that this solver's own SCF iteration (Algorithm 1 with Green
+Iteration) produces for perturbed geometries; the plain superposition of
+atomic orbitals stays the fallback, and plain Green Iteration judges the
+prediction: the SCF run from the predicted start is compared with the run
+from the superposition start.
+
+The orbital model predicts a relative correction y(x) of the normalised
+superposition start s(x): psi_warm = s (1 + y), normalised.  Its training
+target is t = psi* / s - 1 and its loss the quadrature-weighted
+sum_p w_p s_p^2 (y_p - t_p)^2, which is the squared orbital error
+||psi_warm - psi*||_w^2 before normalisation.
+
+The data set of H2 runs: `h2_bond_lengths` (32 seeded bond lengths in
+[1, 2] Bohr), meshes from `workloads.hydrogen_molecule`.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import workloads as W
+
+KT_200K = 200.0 * 3.166811563e-6  # k_B T at 200 K in Ha (Section 6)
+
+
+def _dev(torch, a, device="cuda"):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+
+
+def scf_run(wl, psi0=None, eps0=None, rho0=None, tol_scf=1e-4, max_steps=40, prec=None, store_output=True):
+    """SCF iteration on the device from (psi0, eps0, rho0) (the workload's
+    superposition start where None) until ||rho_out - rho_in||_w < tol_scf.
+    Returns the converged orbitals (host), eigenvalues, energy and the cost:
+    SCF steps and Green iterations.
+
+    store_output: converged orbitals keep their Green step's output.  With
+    Algorithm 2's rule (the step input) an orbital whose first step in an SCF
+    iteration moves it by less than tol_gi is not updated at all, the density
+    residual then falls by mixing alone, and runs from different starts end
+    at energies up to ~1e-4 Ha apart; keeping the output makes every SCF
+    iteration follow V_eff[rho_in], so both starts reach one fixed point."""
+    import torch
+
+    from . import tagi as T
+
+    prec = T.TAGI_FP32C if prec is None else prec
+    m = wl.mesh
+    psi0 = wl.psi if psi0 is None else psi0
+    eps = np.array(wl.eps if eps0 is None else eps0, dtype=np.float64)
+    rho0 = wl.rho if rho0 is None else rho0
+    hist = []
+    t0 = time.perf_counter()
+    with T.Tree(_dev(torch, m.xyz), _dev(torch, m.w), theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size,
+                prec=prec) as tr, T.Scf(tr.handle, wl.n_elec, kT=KT_200K, e_zz=wl.e_zz,
+                                        gi_store_output=store_output) as scf:
+        rho, psi, vx = _dev(torch, rho0), _dev(torch, psi0), _dev(torch, wl.vext)
+        rep = None
+        for _ in range(max_steps):
+            rep = scf.step(vx, wl.vshift, rho, psi, eps)
+            eps = rep["eps"]
+            hist.append({"residual": rep["residual"], "e_total": rep["e_total"], "gi_steps": rep["gi"]["steps"],
+                         "eps": [float(e) for e in eps]})
+            if rep["residual"] < tol_scf:
+                break
+        psi_h = psi.cpu().numpy()
+    torch.cuda.synchronize()
+    return {"psi": psi_h, "eps": np.array(eps), "e_total": rep["e_total"], "converged": rep["residual"] < tol_scf,
+            "scf_steps": len(hist), "gi_steps": int(sum(h["gi_steps"] for h in hist)), "history": hist,
+            "seconds": time.perf_counter() - t0}
+
+
+def generate(bond_lengths, tol_m=3e-6, tol_scf=1e-4, log=print):
+    """Converged H2 runs from the superposition start, one per bond length.
+    Returns a list of records (R, n, mesh weight sum, psi* as float32, eps*,
+    E, cost)."""
+    out = []
+    for R in bond_lengths:
+        wl = W.hydrogen_molecule(float(R), tol_m=tol_m)
+        r = scf_run(wl, tol_scf=tol_scf)
+        psi = r["psi"][0]
+        if np.sum(psi * wl.psi[0] * wl.mesh.w) < 0:  # the sign of an eigenvector is free
+            psi = -psi
+        rec = {"R": float(R), "n": wl.n, "w_sum": float(np.sum(wl.mesh.w)), "psi": psi.astype(np.float32),
+               "eps": float(r["eps"][0]), "e_total": float(r["e_total"]), "converged": bool(r["converged"]),
+               "scf_steps": r["scf_steps"], "gi_steps": r["gi_steps"], "seconds": r["seconds"]}
+        log(f"R {R:.4f} n {wl.n} eps {rec['eps']:.6f} E {rec['e_total']:.6f} scf {rec['scf_steps']} "
+            f"gi {rec['gi_steps']} {rec['seconds']:.2f} s")
+        out.append(rec)
+    return out
+
+
+def save(records, path):
+    np.savez_compressed(path, **{f"{k}_{i}": np.asarray(v) for i, r in enumerate(records) for k, v in r.items()},
+                        count=len(records))
+
+
+def load(path):
+    z = np.load(path)
+    keys = ("R", "n", "w_sum", "psi", "eps", "e_total", "converged", "scf_steps", "gi_steps", "seconds")
+    return [{k: (z[f"{k}_{i}"] if k == "psi" else z[f"{k}_{i}"].item()) for k in keys} for i in range(int(z["count"]))]
+
+
+# ---------------------------------------------------------------- training
+def _nuclei(wl):
+    return np.asarray(wl.meta["nuclei"], dtype=np.float64)
+
+
+def _midpoint_features(T, torch, nuclei):
+    """Features at the midpoint of the two nuclei: a function of the bond
+    length alone, the eigenvalue model's input."""
+    mid = _dev(torch, (0.5 * (nuclei[0] + nuclei[1])).reshape(3, 1))
+    return T.tagi_mlp_features(mid, nuclei)
+
+
+def cosine_lr(lr0, steps):
+    return lambda k: 0.5 * lr0 * (1.0 + np.cos(np.pi * (k - 1) / steps))
+
+
+def train(records, train_idx, steps=3000, lr=3e-3, seed=0, tol_m=3e-6, log=print):
+    """Trains the orbital model on the converged runs records[i], i in
+    train_idx (full-batch Adam on the device, cosine step size), and the
+    eigenvalue model on their eigenvalues.  Returns (orbital Mlp, eigenvalue
+    Mlp, info)."""
+    import torch
+
+    from . import tagi as T
+
+    feats, targets, wts, mids, eps = [], [], [], [], []
+    G = len(train_idx)
+    for i in train_idx:
+        r = records[i]
+        wl = W.hydrogen_molecule(r["R"], tol_m=tol_m)
+        if wl.n != r["n"]:
+            raise RuntimeError(f"mesh of R = {r['R']} has {wl.n} points, the record {r['n']}")
+        s = wl.psi[0]
+        feats.append(T.tagi_mlp_features(_dev(torch, wl.mesh.xyz), _nuclei(wl)))
+        targets.append(torch.tensor((r["psi"].astype(np.float64) / s - 1.0).astype(np.float32), device="cuda"))
+        wts.append(torch.tensor((wl.mesh.w * s * s / G).astype(np.float32), device="cuda"))
+        mids.append(_midpoint_features(T, torch, _nuclei(wl)))
+        eps.append(r["eps"])
+    feat, target, wt = torch.cat(feats), torch.cat(targets), torch.cat(wts)
+    del feats, targets, wts
+    orb = T.Mlp(W.mlp_init(seed))
+    sched = cosine_lr(lr, steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = []
+    for k in range(1, steps + 1):
+        want = k == 1 or k % 500 == 0 or k == steps
+        L = orb.train_step(feat, target, wt, sched(k), want_loss=want)
+        if want:
+            losses.append((k, L))
+    torch.cuda.synchronize()
+    t_orb = time.perf_counter() - t0
+    # eigenvalue model: one "point" per geometry
+    mfeat = torch.cat(mids)
+    et = torch.tensor(np.array(eps, dtype=np.float32), device="cuda")
+    ew = torch.full((G,), 1.0 / G, dtype=torch.float32, device="cuda")
+    eig = T.Mlp(W.mlp_init(seed + 1))
+    for k in range(1, steps + 1):
+        eig.train_step(mfeat, et, ew, sched(k))
+    e_loss = eig.gradient(mfeat, et, ew)[0]
+    info = {"points": int(feat.shape[0]), "geometries": G, "steps": steps, "lr": lr, "losses": losses,
+            "seconds": t_orb, "ms_per_step": 1e3 * t_orb / steps, "eig_rms": float(np.sqrt(e_loss)),
+            "R_range": [min(records[i]["R"] for i in train_idx), max(records[i]["R"] for i in train_idx)]}
+    log(f"trained on {info['points']} points of {G} geometries: loss {losses[0][1]:.3e} -> {losses[-1][1]:.3e}, "
+        f"{info['ms_per_step']:.2f} ms per step; eigenvalue rms {info['eig_rms']:.2e}")
+    return orb, eig, info
+
+
+def predict(orb, eig, wl, R_range=None):
+    """Warm start (psi, eps, rho) for the workload wl, or None when the
+    geometry lies outside the trained range or the prediction is not usable
+    (the superposition start then stays)."""
+    import torch
+
+    from . import tagi as T
+
+    R = wl.meta["R"]
+    if R_range is not None and not (R_range[0] <= R <= R_range[1]):
+        return None
+    feat = T.tagi_mlp_features(_dev(torch, wl.mesh.xyz), _nuclei(wl))
+    psi = orb.warm_start(feat, _dev(torch, wl.psi[0]), _dev(torch, wl.mesh.w)).cpu().numpy()
+    e = float(eig.forward(_midpoint_features(T, torch, _nuclei(wl))).cpu().numpy()[0])
+    if not (np.all(np.isfinite(psi)) and np.isfinite(e) and e + wl.vshift < 0.0):
+        return None
+    return psi, e, wl.n_elec * psi * psi
+
+
+def evaluate(orb, eig, records, test_idx, R_range=None, tol_m=3e-6, tol_scf=1e-4, log=print):
+    """SCF runs of the held-out geometries from the superposition start and
+    from the predicted start; the converged run is the judge of both."""
+    rows = []
+    for i in test_idx:
+        r = records[i]
+        wl = W.hydrogen_molecule(r["R"], tol_m=tol_m)
+        w = wl.mesh.w
+        ref = r["psi"].astype(np.float64)
+        base = scf_run(wl, tol_scf=tol_scf)
+        pred = predict(orb, eig, wl, R_range)
+        if pred is None:
+            warm, used = base, False
+            e_pred, err_pred = float("nan"), float("nan")
+        else:
+            psi, e_pred, rho = pred
+            warm, used = scf_run(wl, psi0=psi[None], eps0=[e_pred], rho0=rho, tol_scf=tol_scf), True
+            err_pred = float(np.sqrt(np.sum((psi - ref) ** 2 * w)))
+        row = {"R": r["R"], "n": wl.n, "used_prediction": used,
+               "orbital_error": {"superposition": float(np.sqrt(np.sum((wl.psi[0] - ref) ** 2 * w))),
+                                 "predicted": err_pred},
+               "eps": {"converged": r["eps"], "predicted": e_pred, "superposition_guess": float(wl.eps[0])},
+               "scf_steps": {"superposition": base["scf_steps"], "predicted": warm["scf_steps"]},
+               "green_iterations": {"superposition": base["gi_steps"], "predicted": warm["gi_steps"]},
+               "seconds": {"superposition": base["seconds"], "predicted": warm["seconds"]},
+               "e_total": {"superposition": base["e_total"], "predicted": warm["e_total"]},
+               "converged": bool(base["converged"] and warm["converged"])}
+        log(f"R {r['R']:.4f}: orbital error {row['orbital_error']['superposition']:.3e} -> {err_pred:.3e}; "
+            f"SCF steps {base['scf_steps']} -> {warm['scf_steps']}, Green iterations {base['gi_steps']} -> "
+            f"{warm['gi_steps']}; E {base['e_total']:.7f} / {warm['e_total']:.7f}")
+        rows.append(row)
+    return rows
+
+
+def split(count=32):
+    """Held-out geometries: every fourth bond length in sorted order."""
+    test = list(range(1, count, 4))
+    return [i for i in range(count) if i not in test], test
+
+
+def main(argv=None):
+    """python -m paper_2003_01833_gb300.warmstart [--data file.npz] [--steps K]
+    runs the H2 data set (or loads it), trains both models, evaluates the
+    held-out geometries and prints one JSON object."""
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--data", default=None, help="npz from a previous run (else generated here)")
+    ap.add_argument("--save", default=None, help="write the generated data set here")
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    a = ap.parse_args(argv)
+    import sys
+
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    Rs = W.h2_bond_lengths()
+    t0 = time.perf_counter()
+    records = load(a.data) if a.data else generate(Rs, log=log)
+    t_gen = time.perf_counter() - t0
+    if a.save and not a.data:
+        save(records, a.save)
+    tr, te = split(len(records))
+    orb, eig, info = train(records, tr, steps=a.steps, lr=a.lr, log=log)
+    rows = evaluate(orb, eig, records, te, R_range=info["R_range"], log=log)
+    orb.close()
+    eig.close()
+    tot = lambda key, k: int(sum(r[key][k] for r in rows))
+    out = {"data": {"molecule": "H2", "geometries": len(records), "bond_lengths": [r["R"] for r in records],
+                    "points": [r["n"] for r in records], "seconds": t_gen,
+                    "all_converged": all(bool(r["converged"]) for r in records)},
+           "train": info, "test": rows,
+           "totals": {"scf_steps": {"superposition": tot("scf_steps", "superposition"),
+                                    "predicted": tot("scf_steps", "predicted")},
+                      "green_iterations": {"superposition": tot("green_iterations", "superposition"),
+                                           "predicted": tot("green_iterations", "predicted")},
+                      "max_energy_difference": max(abs(r["e_total"]["superposition"] - r["e_total"]["predicted"])
+                                                   for r in rows)}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -82,3 +82,35 @@ def test_new_entry_points_validate_without_gpu(lib):
     eps = (ctypes.c_double * 1)(-0.5)
     assert L.tagi_scf_step(None, None, 0.0, None, None, eps, 1, None, None, None, None) == T.TAGI_ERR_INVALID_ARG
     assert L.tagi_scf_destroy(None) == T.TAGI_OK
+
+
+def test_warm_start_entry_points_validate_without_gpu(lib):
+    """The MLP calls reject bad arguments before touching a device."""
+    import numpy as np
+
+    import paper_2003_01833_gb300.tagi as T
+
+    L = T.lib()
+    h = ctypes.c_void_p()
+    p = np.zeros(T.MLP_PARAMS)
+    D = ctypes.POINTER(ctypes.c_double)
+    assert L.tagi_mlp_create(7, 32, p.ctypes.data_as(D), p.size, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+    assert L.tagi_mlp_create(8, 64, p.ctypes.data_as(D), p.size, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+    assert L.tagi_mlp_create(8, 32, p.ctypes.data_as(D), p.size - 1, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+    q = p.copy()
+    q[5] = np.nan
+    assert L.tagi_mlp_create(8, 32, q.ctypes.data_as(D), q.size, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+    assert "finite" in L.tagi_last_error().decode()
+    nuc = np.array([[0.0, 0, 0], [1.0, 0, 0]])
+    fake = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    assert L.tagi_mlp_features(fake, 10, nuc.ctypes.data_as(D), 1, fake, None) == T.TAGI_ERR_INVALID_ARG
+    same = np.zeros((2, 3))
+    assert L.tagi_mlp_features(fake, 10, same.ctypes.data_as(D), 2, fake, None) == T.TAGI_ERR_INVALID_ARG
+    assert L.tagi_mlp_features(fake, 10, nuc.ctypes.data_as(D), 2, ctypes.c_void_p(18), None) \
+        == T.TAGI_ERR_INVALID_ARG  # feat not 16-byte aligned
+    assert L.tagi_mlp_features(fake, 0, nuc.ctypes.data_as(D), 2, fake, None) == T.TAGI_ERR_INVALID_ARG
+    assert L.tagi_mlp_forward(None, fake, 10, fake, None) == T.TAGI_ERR_INVALID_ARG
+    a = T.tagi_adam_params(1e-3, 0.9, 0.999, 1e-8)
+    assert L.tagi_mlp_train_step(None, fake, fake, fake, 10, ctypes.byref(a), None, None) == T.TAGI_ERR_INVALID_ARG
+    assert L.tagi_mlp_warm_start(None, fake, fake, fake, 10, fake, None) == T.TAGI_ERR_INVALID_ARG
+    assert L.tagi_mlp_destroy(None) == T.TAGI_OK

@@ -60,7 +60,10 @@ def _gpu_loop(T, wl, psi0, eps0, vshift, prec, **kw):
     return out
 
 
-def test_plain_loop_matches_oracle_with_a_convergence_event(T, hcase):
+@pytest.mark.parametrize("store_output", [False, True])
+def test_plain_loop_matches_oracle_with_a_convergence_event(T, hcase, store_output):
+    """A convergence event of orbital 0; the converged orbital keeps its step
+    input (Algorithm 2) or, with store_output, its step output."""
     wl, psi0, eps0, otree = hcase
     w = wl.mesh.w
     free = oracle.green_iterate(otree, 0.7, 6, w, wl.veff, -0.5, psi0, eps0, tol_gi=0.0, max_iter=8, mix_tol=0.0)
@@ -73,9 +76,11 @@ def test_plain_loop_matches_oracle_with_a_convergence_event(T, hcase):
 
     k = next(k for k in range(2, 7) if ok(k))
     tol = float(np.sqrt(tr[k - 1, 0] * tr[k, 0]))
-    ref = oracle.green_iterate(otree, 0.7, 6, w, wl.veff, -0.5, psi0, eps0, tol_gi=tol, max_iter=8, mix_tol=0.0)
+    ref = oracle.green_iterate(otree, 0.7, 6, w, wl.veff, -0.5, psi0, eps0, tol_gi=tol, max_iter=8, mix_tol=0.0,
+                               store_output=store_output)
     assert ref["iters"][0] == k + 1 and ref["iters"][1] == -1
-    out = _gpu_loop(T, wl, psi0, eps0, -0.5, T.TAGI_FP64, tol_gi=tol, max_iter=8, mix_tol=0.0)
+    out = _gpu_loop(T, wl, psi0, eps0, -0.5, T.TAGI_FP64, tol_gi=tol, max_iter=8, mix_tol=0.0,
+                    store_output=store_output)
     np.testing.assert_array_equal(out["iters"], ref["iters"])
     assert out["steps"] == ref["steps"] and out["field_steps"] == ref["field_steps"]
     assert out["n_converged"] == 1

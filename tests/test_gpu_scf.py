@@ -161,3 +161,30 @@ def test_carbon_monoxide_scf_reaches_the_papers_energy(T):
     np.testing.assert_allclose(rep["occ"][:7], 1.0, atol=1e-9)
     assert rep["occ"][7] < 1e-9
     assert np.all(np.diff(eps) >= -1e-6) and eps[-1] < 0
+
+
+def test_lithium_scf_with_stored_outputs_reaches_the_papers_energy_closer(T):
+    """The same Li SCF with gi_store_output: a converged orbital keeps its
+    Green step's output, so every SCF iteration follows V_eff[rho_in] (with
+    Algorithm 2's stored input an orbital that one step moves by less than
+    tol_gi is not updated, and the density residual then falls by mixing
+    alone).  Measured: 0.29 mHa from E_ref in 6 SCF steps, against 1.0 mHa
+    in 8 with the stored input; the bound here is 1 mHa."""
+    wl = W.lithium()
+    m = wl.mesh
+    with T.Tree(dev(m.xyz), dev(m.w), theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size,
+                prec=T.TAGI_FP32C) as tr, T.Scf(tr.handle, wl.n_elec, kT=KT_200K, e_zz=wl.e_zz,
+                                                gi_store_output=True) as scf:
+        rho, psi, vx = dev(wl.rho), dev(wl.psi), dev(wl.vext)
+        eps = wl.eps
+        hist = []
+        for _ in range(30):
+            rep = scf.step(vx, wl.vshift, rho, psi, eps)
+            eps = rep["eps"]
+            hist.append((rep["residual"], rep["e_total"], rep["gi"]["steps"]))
+            if rep["residual"] < 1e-4:
+                break
+    print("Li SCF, stored outputs (residual, E, GI steps):", hist)
+    assert hist[-1][0] < 1e-4
+    assert abs(hist[-1][1] - E_REF_LI) < 1e-3
+    assert eps[0] < eps[1] < 0
