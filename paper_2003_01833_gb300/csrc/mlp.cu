@@ -320,11 +320,17 @@ __global__ void __launch_bounds__(256) k_warm_apply(const float* __restrict__ y,
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// psi /= sqrt(sum of the partials): one thread of each block sums them in
+// block order (every block gets the same value) and shares the factor.
 __global__ void k_warm_scale(double* __restrict__ psi, int64_t n, const double* __restrict__ part, int nblk)
 {
-    double s = 0.0;
-    for (int b = 0; b < nblk; b++) s += part[b];
-    const double inv = 1.0 / sqrt(s);
+    __shared__ double inv;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; b++) s += part[b];
+        inv = 1.0 / sqrt(s);
+    }
+    __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         psi[i] *= inv;
 }

@@ -232,10 +232,40 @@ def split(count=32):
     return [i for i in range(count) if i not in test], test
 
 
+def profile_case(steps=3):
+    """The kernels of the warm start on one H2 mesh (R = 1.4 Bohr, 192,000
+    points): features, `steps` training steps against a smooth synthetic
+    target, inference and the warm start.  The command ncu wraps; prints
+    the measured ms per training step."""
+    import torch
+
+    from . import tagi as T
+
+    wl = W.hydrogen_molecule(1.4)
+    s = wl.psi[0]
+    feat = T.tagi_mlp_features(_dev(torch, wl.mesh.xyz), _nuclei(wl))
+    r = np.sqrt((wl.mesh.xyz ** 2).sum(0))
+    target = torch.tensor((0.2 * np.tanh(r - 1.0)).astype(np.float32), device="cuda")
+    wt = torch.tensor((wl.mesh.w * s * s).astype(np.float32), device="cuda")
+    with T.Mlp(W.mlp_init(0)) as m:
+        m.train_step(feat, target, wt, 1e-3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            m.train_step(feat, target, wt, 1e-3)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0) / steps
+        m.forward(feat)
+        m.warm_start(feat, _dev(torch, s), _dev(torch, wl.mesh.w))
+        torch.cuda.synchronize()
+    print(f"profile case: {wl.n} points, {ms:.3f} ms per training step")
+
+
 def main(argv=None):
     """python -m paper_2003_01833_gb300.warmstart [--data file.npz] [--steps K]
     runs the H2 data set (or loads it), trains both models, evaluates the
-    held-out geometries and prints one JSON object."""
+    held-out geometries and prints one JSON object.  --profile-case runs
+    only the kernels on one mesh (the command ncu wraps)."""
     import argparse
     import json
 
@@ -244,7 +274,11 @@ def main(argv=None):
     ap.add_argument("--save", default=None, help="write the generated data set here")
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--profile-case", action="store_true")
     a = ap.parse_args(argv)
+    if a.profile_case:
+        profile_case()
+        return
     import sys
 
     log = lambda m: print(m, file=sys.stderr, flush=True)
