@@ -30,7 +30,12 @@ constexpr int kThreads = 128;
 // Stash row of one point for the gradient reduction: x | h1 | h2 | dz1 | dz2 |
 // dy | 1.  An odd stride keeps the rows of a warp's 32 points in 32 banks.
 constexpr int cX = 0, cH1 = 8, cH2 = 40, cD1 = 72, cD2 = 104, cDy = 136, cOne = 137, kStride = 139;
-constexpr int kEntries = (kP + kThreads - 1) / kThreads;  // gradient entries per thread
+// Gradient entries per thread: a 2 x 4 tile of W2 (rows j0, j0+1; columns
+// i0..i0+3), 6 shared loads per point for its 8 products, and up to 3 of the
+// other 353 entries (W1, b1, b2, W3, b3), 2 loads per product.
+constexpr int kRest = kP - kH * kH;
+constexpr int kRestPer = (kRest + kThreads - 1) / kThreads;
+static_assert(kThreads == (kH / 2) * (kH / 4), "one 2 x 4 tile of W2 per thread");
 constexpr int kMaxNuclei = 16;
 constexpr size_t kGradSmem = sizeof(float) * (kPPad + (size_t)kThreads * kStride);
 
@@ -166,8 +171,9 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(const uint16_t* __rest
 // Loss L = sum_p wt_p (y_p - t_p)^2 and its gradient: each thread runs the
 // forward and backward pass of one point of a 128-point tile and stashes
 // (x, h1, h2, dz1, dz2, dy) in shared memory; then each thread forms its own
-// gradient entries (outer-product sums over the tile in point order, float32)
-// and adds them to float64 accumulators.  Tiles are strided over a fixed
+// gradient entries (outer-product sums over the tile in point order, float32;
+// a 2 x 4 register tile of W2 and up to 3 other entries) and adds them to
+// float64 accumulators.  Tiles are strided over a fixed
 // grid; per-block partials [grid][kP + 1] (the loss last) are reduced by
 // k_mlp_adam in block order.
 __global__ void __launch_bounds__(kThreads) k_mlp_grad(const uint16_t* __restrict__ feat,
@@ -182,28 +188,30 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const uint16_t* __restric
     const int tid = threadIdx.x;
     load_params(sw, master);
 
-    int ca[kEntries], cb[kEntries];
-    double acc[kEntries];
+    const int j0 = 2 * (tid >> 3), i0 = 4 * (tid & 7);
+    double accw[8];
+    int ca[kRestPer], cb[kRestPer], ce[kRestPer];
+    double acc[kRestPer];
 #pragma unroll
-    for (int k = 0; k < kEntries; k++) {
-        const int e = tid + k * kThreads;
-        int a = cDy, b = cOne;  // entries past kP: computed, never written
-        if (e < oB1) {
-            a = cD1 + e / kF;
-            b = cX + e % kF;
-        } else if (e < oW2) {
-            a = cD1 + (e - oB1);
-            b = cOne;
-        } else if (e < oB2) {
-            a = cD2 + (e - oW2) / kH;
-            b = cH1 + (e - oW2) % kH;
-        } else if (e < oW3) {
-            a = cD2 + (e - oB2);
-            b = cOne;
-        } else if (e < oB3) {
-            a = cDy;
-            b = cH2 + (e - oW3);
+    for (int k = 0; k < 8; k++) accw[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < kRestPer; k++) {
+        const int q = tid + k * kThreads;  // index among the entries outside W2
+        int e = -1, a = cDy, b = cOne;     // q >= kRest: computed, never written
+        if (q < oW2) {                     // W1 and b1 precede W2
+            e = q;
+            a = cD1 + (q < oB1 ? q / kF : q - oB1);
+            b = q < oB1 ? cX + q % kF : cOne;
+        } else if (q < oW2 + kH) {         // b2
+            e = oB2 + (q - oW2);
+            a = cD2 + (q - oW2);
+        } else if (q < oW2 + 2 * kH) {     // W3
+            e = oW3 + (q - oW2 - kH);
+            b = cH2 + (q - oW2 - kH);
+        } else if (q < kRest) {            // b3
+            e = oB3;
         }
+        ce[k] = e;
         ca[k] = a;
         cb[k] = b;
         acc[k] = 0.0;
@@ -251,20 +259,40 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const uint16_t* __restric
             for (int c = 0; c < kStride; c++) row[c] = 0.0f;
         }
         __syncthreads();
+        {
+            float s[8], r[kRestPer];
 #pragma unroll
-        for (int k = 0; k < kEntries; k++) {
-            float s = 0.0f;
-            for (int p = 0; p < kThreads; p++) s = fmaf(st[p * kStride + ca[k]], st[p * kStride + cb[k]], s);
-            acc[k] += (double)s;
+            for (int k = 0; k < 8; k++) s[k] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kRestPer; k++) r[k] = 0.0f;
+            for (int p = 0; p < kThreads; p++) {
+                const float* rp = st + p * kStride;
+                const float d0 = rp[cD2 + j0], d1 = rp[cD2 + j0 + 1];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float h = rp[cH1 + i0 + c];
+                    s[c] = fmaf(d0, h, s[c]);
+                    s[4 + c] = fmaf(d1, h, s[4 + c]);
+                }
+#pragma unroll
+                for (int k = 0; k < kRestPer; k++) r[k] = fmaf(rp[ca[k]], rp[cb[k]], r[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) accw[k] += (double)s[k];
+#pragma unroll
+            for (int k = 0; k < kRestPer; k++) acc[k] += (double)r[k];
         }
         __syncthreads();
     }
     double* out = partial + (size_t)blockIdx.x * (kP + 1);
 #pragma unroll
-    for (int k = 0; k < kEntries; k++) {
-        const int e = tid + k * kThreads;
-        if (e < kP) out[e] = acc[k];
+    for (int c = 0; c < 4; c++) {
+        out[oW2 + j0 * kH + i0 + c] = accw[c];
+        out[oW2 + (j0 + 1) * kH + i0 + c] = accw[4 + c];
     }
+#pragma unroll
+    for (int k = 0; k < kRestPer; k++)
+        if (ce[k] >= 0) out[ce[k]] = acc[k];
     sl[tid] = lsum;
     __syncthreads();
     if (tid == 0) {
