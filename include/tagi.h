@@ -195,7 +195,7 @@ int64_t tagi_kernel_launches(void);
 /* Device memory of trees and calls comes from a caching allocator: blocks a
  * tree or a call gives back are kept for later calls on the same stream.
  * tagi_trim_cache synchronises the device and returns every cached block to
- * the driver (call it after destroying trees to shrink the footprint). */
+ * the CUDA driver (call it after destroying trees to shrink the footprint). */
 tagi_status tagi_trim_cache(void);
 
 /* Mean relative bias of the float32 kernel values of the TAGI_FP32C path on
@@ -370,7 +370,7 @@ tagi_status tagi_scf_destroy(tagi_scf* scf);
  * features of a mesh point to a relative correction y of the normalised
  * superposition start s: psi = s (1 + y), normalised in the quadrature
  * norm.  Trained on converged orbitals of this solver's SCF runs; plain
- * Green Iteration judges its error.
+ * Green Iteration measures its error.
  *
  * Model: F = 8 features, two tanh layers of H = 32 units, one output.
  * Parameters (1377 float64 values, this order): W1 (H x F row-major), b1 (H),

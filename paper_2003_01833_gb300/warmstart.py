@@ -4,7 +4,7 @@ the nuclei and the superposed atomic Slater orbitals), and a second one that
 predicts the eigenvalue from the bond length.  Both are trained on converged
 orbitals that this solver's own SCF iteration (Algorithm 1 with Green
 Iteration) produces for perturbed geometries; the plain superposition of
-atomic orbitals stays the fallback, and plain Green Iteration judges the
+atomic orbitals stays the fallback, and plain Green Iteration measures the
 prediction: the SCF run from the predicted start is compared with the run
 from the superposition start.
 
@@ -194,7 +194,7 @@ def predict(orb, eig, wl, R_range=None):
 
 def evaluate(orb, eig, records, test_idx, R_range=None, tol_m=3e-6, tol_scf=1e-4, log=print):
     """SCF runs of the held-out geometries from the superposition start and
-    from the predicted start; the converged run is the judge of both."""
+    from the predicted start; the converged runs measure both starts."""
     rows = []
     for i in test_idx:
         r = records[i]

@@ -1,5 +1,5 @@
 """The learned warm start on the device (tagi_mlp_*) against the oracle
-(oracle/mlp.py), and judged by the SCF iteration.
+(oracle/mlp.py), and measured by the SCF iteration.
 
 - Features: bit-exact bfloat16 encodings (both sides form them in float64,
   in the same operation order, and round once, ties to even).
@@ -12,7 +12,7 @@
 - Adam: float64 on both sides: one step from a given gradient to 1e-14.
 - Training: 40 full-batch steps follow the oracle's loss curve to 1e-3.
 - Warm start: psi = s (1 + y) normalised, to 1e-5 relative.
-- Judge: trained on three H2 geometries, the predicted start for a fourth
+- SCF measure: trained on three H2 geometries, the predicted start for a fourth
   is closer to the converged orbital than the superposition start, and the
   SCF from it converges to the same energy in no more Green iterations.
 """
@@ -145,7 +145,7 @@ def test_warm_start_against_oracle(T):
     assert abs(np.sum(psi * psi * wl.mesh.w) - 1.0) < 1e-12
 
 
-def test_predicted_start_is_judged_by_the_scf(T):
+def test_predicted_start_is_measured_by_the_scf(T):
     from paper_2003_01833_gb300 import warmstart as WS
 
     records = WS.generate([1.2, 1.4, 1.6, 1.5], log=print)
