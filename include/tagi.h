@@ -380,6 +380,9 @@ tagi_status tagi_scf_destroy(tagi_scf* scf);
  * float64 in a fixed order (deterministic on a given device); Adam (Kingma
  * and Ba, 2015) updates float64 master weights.
  *
+ * A tagi_mlp holds its weights, Adam moments and scratch: use it from one
+ * stream at a time.
+ *
  * Features of a point (float64, then rounded to bfloat16, stored as (n, 8)
  * uint16 encodings, row-major, 16-byte aligned): with r1 <= r2 the
  * distances to the two nearest nuclei (lower index first on ties) and R the
