@@ -114,3 +114,24 @@ def test_warm_start_entry_points_validate_without_gpu(lib):
     assert L.tagi_mlp_train_step(None, fake, fake, fake, 10, ctypes.byref(a), None, None) == T.TAGI_ERR_INVALID_ARG
     assert L.tagi_mlp_warm_start(None, fake, fake, fake, 10, fake, None) == T.TAGI_ERR_INVALID_ARG
     assert L.tagi_mlp_destroy(None) == T.TAGI_OK
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/tagi.h compiles as pedantic C99: the boundary needs no C++."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "include/tagi.h"\n'
+                   "int main(void) {\n"
+                   "    tagi_gi_params g = {1e-5, 10, 0.5, 5, 1.0, 0};\n"
+                   "    tagi_adam_params a = {1e-3, 0.9, 0.999, 1e-8};\n"
+                   "    (void)g; (void)a;\n"
+                   "    return tagi_version() == 0;\n"
+                   "}\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-I", ROOT,
+                        str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
