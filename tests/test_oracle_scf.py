@@ -8,6 +8,15 @@ total-energy-gradient-free; LDA of Section 2).
   generator's independent implementation (rho^(1/3) form); the correlation
   potential is the density derivative of rho eps_c; the exchange energy of a
   Gaussian density against its closed form on an adaptive mesh.
+- Perdew-Zunger correlation against what fixes it from outside the fit:
+  the Gell-Mann-Brueckner high-density slope (1 - ln 2)/pi^2, the Wigner
+  low-density limit (bcc Madelung energy -0.89593/r_s for exchange plus
+  correlation), the Vosko-Wilk-Nusair parametrisation of the same
+  Ceperley-Alder data (a different functional form), and the smooth join of
+  its two branches at r_s = 1 that Perdew and Zunger imposed.
+- The gradient-free energy assembly on a one-electron case whose Kohn-Sham
+  energy is known in closed form (1s density, potential built so that the
+  1s orbital is the exact eigenfunction).
 - Hartree energy term of the SCF potentials against the Gaussian closed form.
 - One SCF step of the hydrogen atom: the density integrates to N_e, a lone
   orbital holding one electron has mu = eps and f = 1/2, the first density
@@ -84,6 +93,64 @@ def test_lda_independent_forms_agree_and_potential_is_derivative():
     np.testing.assert_allclose(vc, num, rtol=1e-7, atol=1e-12)
 
 
+def _rs_to_rho(rs):
+    return 3.0 / (4.0 * np.pi * np.asarray(rs, np.float64) ** 3)
+
+
+def _vwn5(rs):
+    """Vosko-Wilk-Nusair (1980) fit 'V' of the Ceperley-Alder correlation
+    energy of the unpolarised electron gas, in Ha: x = sqrt(r_s),
+    X(x) = x^2 + b x + c, Q = sqrt(4c - b^2)."""
+    A, x0, b, c = 0.0310907, -0.10498, 3.72744, 12.9352
+    x = np.sqrt(rs)
+    X = lambda t: t * t + b * t + c
+    Q = math.sqrt(4 * c - b * b)
+    at = np.arctan(Q / (2 * x + b))
+    return A * (np.log(x * x / X(x)) + 2 * b / Q * at
+                - b * x0 / X(x0) * (np.log((x - x0) ** 2 / X(x)) + 2 * (b + 2 * x0) / Q * at))
+
+
+def test_pz_high_density_slope_is_gell_mann_brueckner():
+    # eps_c -> A ln r_s + const as r_s -> 0 with A = (1 - ln 2)/pi^2 (random
+    # phase approximation; Perdew and Zunger round it to 0.0311 Ha)
+    a_gmb = (1.0 - math.log(2.0)) / math.pi**2
+    for rs in (1e-6, 1e-8):
+        h = 1e-3
+        e = oracle.lda_correlation(_rs_to_rho([rs * math.exp(-h), rs * math.exp(h)]))[0]
+        slope = (e[1] - e[0]) / (2 * h)
+        assert abs(slope - a_gmb) < 1e-3 * a_gmb, (rs, slope, a_gmb)
+
+
+def test_pz_low_density_limit_is_wigner():
+    # exchange plus correlation of the electron gas at very low density tends
+    # to the Madelung energy of the bcc Wigner crystal, -0.89593 / r_s
+    rs = 1e8
+    exc, _ = oracle.lda_xc(_rs_to_rho([rs]))
+    assert abs(exc[0] * rs + 0.89593) < 0.02 * 0.89593, exc[0] * rs
+
+
+def test_pz_agrees_with_vwn_parametrisation():
+    # two fits of the same quantum Monte Carlo data by different functional
+    # forms: a swapped r_s branch or a wrong constant moves PZ off VWN
+    rs = np.geomspace(0.05, 100.0, 60)
+    ec, _ = oracle.lda_correlation(_rs_to_rho(rs))
+    ref = _vwn5(rs)
+    assert np.max(np.abs(ec - ref)) < 1.5e-3
+    assert np.max(np.abs(ec - ref) / np.abs(ref)) < 0.02
+    # spot values of the VWN form itself (r_s = 1, 2, 5; in Ha)
+    np.testing.assert_allclose(_vwn5(np.array([1.0, 2.0, 5.0])), [-0.060019, -0.044783, -0.028134], atol=2e-6)
+
+
+def test_pz_branches_join_smoothly_at_rs_one():
+    d = 1e-7
+    e = oracle.lda_correlation(_rs_to_rho([1.0 - 2 * d, 1.0 - d, 1.0 + d, 1.0 + 2 * d]))[0]
+    # value and slope on both sides of r_s = 1 (Perdew and Zunger chose the
+    # high-density C and D for continuity)
+    assert abs(e[1] - e[2]) < 1e-4
+    s_lo, s_hi = (e[1] - e[0]) / d, (e[3] - e[2]) / d
+    assert abs(s_lo - s_hi) < 1e-3 * abs(s_hi), (s_lo, s_hi)
+
+
 @pytest.fixture(scope="module")
 def hmesh():
     wl = W.hydrogen_adaptive()
@@ -123,3 +190,45 @@ def test_one_scf_step_of_hydrogen(hmesh):
     assert E["total"] == E["band"] - E["hartree"] + E["xc"] - E["vxc"] + E["zz"]
     assert -0.35 < out["eps"][0] < -0.15
     assert len(mix["x"]) == 1
+
+
+def test_gradient_free_energy_closed_form_one_electron():
+    """One electron with the 1s density rho = e^{-2r}/pi.  V_ext is chosen as
+    -1/r - V_H[rho] - V_xc[rho] with the exact Hartree potential of rho,
+    1/r - e^{-2r}(1 + 1/r), so V_eff = -1/r up to the treecode and mesh
+    error and the 1s orbital is the eigenfunction with eps = -1/2.  The
+    Kohn-Sham energy (kinetic + external + Hartree + xc + E_ZZ) is then known
+    from closed forms and 1D radial integrals:
+      T_s = 1/2, <V_ext, rho> = -1 - 2 E_H - <V_xc, rho>, E_H = 5/16,
+      E_x = -(81/256) 3^(1/3) / pi^(2/3), <v_x, rho> = 4/3 E_x,
+    and E_c, <v_c, rho> by quadrature over r.  The gradient-free energy of
+    the SCF step must equal it.  A sign slip on any double-counting term or
+    a missing factor of 2 in the band energy moves it by >= 0.2 Ha."""
+    import scipy.integrate
+
+    wl = W.hydrogen_adaptive(tol_m=1e-4)
+    T = oracle.Tree(wl.mesh.xyz, 2000)
+    w = wl.mesh.w
+    r = np.sqrt(np.sum(wl.mesh.xyz**2, axis=0))
+    rho = np.exp(-2 * r) / np.pi
+    vh_exact = 1.0 / r - np.exp(-2 * r) * (1.0 + 1.0 / r)
+    _, vxc = oracle.lda_xc(rho)
+    vext = -1.0 / r - vh_exact - vxc
+    psi = np.exp(-r) / np.sqrt(np.sum(np.exp(-2 * r) * w))
+    e_zz = 0.7
+    out = oracle.scf_step(T, 0.7, 6, w, vext, rho, psi[None], np.array([-0.45]), 0.0, 1.0, 6.3336e-4, e_zz,
+                          tol_gi=1e-6, max_iter=60, mix={})
+    rad = lambda fn: scipy.integrate.quad(lambda x: 4 * np.pi * x * x * fn(x), 0, 60, limit=400, epsabs=1e-13)[0]
+    rho_r = lambda x: np.exp(-2 * x) / np.pi
+    e_x = -(81.0 / 256.0) * 3 ** (1 / 3) / np.pi ** (2 / 3)
+    e_c = rad(lambda x: oracle.lda_correlation(np.array([rho_r(x)]))[0][0] * rho_r(x))
+    vc_rho = rad(lambda x: oracle.lda_correlation(np.array([rho_r(x)]))[1][0] * rho_r(x))
+    e_h = 5.0 / 16.0
+    e_xc, e_vxc = e_x + e_c, 4.0 / 3.0 * e_x + vc_rho
+    t_s, e_ext = 0.5, -1.0 - 2.0 * e_h - e_vxc
+    e_ks = t_s + e_ext + e_h + e_xc + e_zz
+    E = out["energy"]
+    assert abs(out["eps"][0] + 0.5) < 2e-3
+    assert abs(E["hartree"] - e_h) < 2e-4
+    assert abs(E["xc"] - e_xc) < 2e-4 and abs(E["vxc"] - e_vxc) < 2e-4
+    assert abs(E["total"] - e_ks) < 3e-3, (E["total"], e_ks)
