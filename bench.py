@@ -165,7 +165,10 @@ class ClockSampler:
 # shared-memory loads, the self-pair mask, the two-float folds and loop
 # overhead excluded), see kernel_work.
 ISSUE_PER_SM_CLK = 128  # 4 schedulers x 32 lanes, one warp instruction each per clock
-XU_EX2_PER_SM_CLK = 30.1  # measured ex2.approx rate per SM per clock on the GB300; rsqrt.approx runs at half
+# ex2.approx per SM per clock: measured live by tagi_unit_rates (the value
+# below, from the same measurement on a GB300, serves only when none is given)
+XU_EX2_PER_SM_CLK = 30.1
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tf32 : bf16 tensor throughput of the GB300
 
 
 def kernel_work(info, ny, hh):
@@ -189,7 +192,7 @@ def kernel_work(info, ny, hh):
     return instr, xu
 
 
-def roofline(info, nfields_y, hh, kernel_ms, clk_mhz, sms):
+def roofline(info, nfields_y, hh, kernel_ms, clk_mhz, sms, xu_rate=XU_EX2_PER_SM_CLK):
     """ALU roofline of k_interact32: the tighter of the issue bound (128
     instructions per SM per clock) and the MUFU bound (measured ex2 rate).
     Fields go to the kernel in launch groups of up to 8 (the Hartree field
@@ -209,93 +212,163 @@ def roofline(info, nfields_y, hh, kernel_ms, clk_mhz, sms):
     inter = (info["near_pairs"] + info["far_pairs"]) * nf
     f = clk_mhz * 1e6
     peak_issue = sms * ISSUE_PER_SM_CLK * f * inter / instr
-    peak_xu = sms * XU_EX2_PER_SM_CLK * f * inter / xu
+    peak_xu = sms * xu_rate * f * inter / xu
     achieved = inter / (kernel_ms * 1e-3)
     return achieved, min(peak_issue, peak_xu), {"issue_bound": peak_issue, "mufu_bound": peak_xu,
                                                 "instr_per_interaction": instr / inter,
                                                 "mufu_ex2_units_per_interaction": xu / inter}
 
 
+def measured_peaks():
+    """MEASURED_PEAKS.json (driver-written) or None."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return None
+
+
 def anterp_line(info, ncols, prof, steps, clk_mhz, sms):
-    """Anterpolation of the step's fields (a4): algorithmic 2 P N_S flops per
-    column summed over the approximated clusters, over the phase time, against
-    the FP32 FMA peak (128 lanes x 2 flops per SM per clock)."""
+    """Anterpolation of the step's fields (a4) on the tensor cores (3xTF32):
+    algorithmic 2 P N_S flops per column summed over the approximated
+    clusters, over the phase time, against the tf32 tensor peak (the measured
+    bf16 peak x the nominal tf32 : bf16 ratio); the split precision executes 3x
+    the algorithmic flops.  Also against the FP32 FMA peak, the bound of a
+    SIMT form."""
     ms = prof["anterp"][0] / max(1, steps)
     flops = 2.0 * info["n_proxies"] * info["ant_points"] * ncols
-    peak = sms * 128 * 2 * clk_mhz * 1e6
-    return {"ms_per_step": ms, "algorithmic_flops": flops, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
-            "fp32_fma_peak_tflops": peak / 1e12, "frac": flops / (ms * 1e-3) / peak,
-            "note": "float64 basis evaluation per point and dimension is not counted; phase includes the "
-                    "two-float split of the fields and the per-cluster reduction"}
+    achieved = flops / (ms * 1e-3)
+    fma_peak = sms * 128 * 2 * clk_mhz * 1e6
+    mp = measured_peaks()
+    bf16 = (mp or {}).get("bf16_tflops") or 1900.0
+    tf32 = bf16 * TF32_PER_BF16 * 1e12
+    return {"ms_per_step": ms, "algorithmic_flops": flops, "achieved_tflops": achieved / 1e12,
+            "tf32_peak_tflops": tf32 / 1e12, "frac_tf32": achieved / tf32, "frac_tf32_executed": 3 * achieved / tf32,
+            "tf32_peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops" if mp else "of fallback: 1.9 PFLOP/s")
+                                + " x 1.1/2.25 nominal",
+            "fp32_fma_peak_tflops": fma_peak / 1e12, "frac_fp32_fma": achieved / fma_peak,
+            "note": "phase = charge split and tiling, 3xTF32 tcgen05 contraction with two-float folds, per-cluster "
+                    "reduction; the basis rows are cached with the tree"}
 
 
 # ------------------------------------------------------------------ oracle legs
-def cpu_oracle_rate(wl, budget_s=20.0, seed=0, nthreads=0):
-    """Oracle (float64 CPU treecode, as it stands, OpenMP on every core) on a
-    bounded sample of the same workload: a seeded sample of target batches,
-    all three fields.  The oracle anterpolates every cluster on each call; that
-    cost is timed on its own (a call with no batch) and charged to the sample
-    in proportion to its share of the batches, as a full run would amortise it.
-    Returns interactions/s, threads used and a description of the sample."""
-    import oracle
+def workload_name(wl):
+    """The workload string both arms print in config.workload."""
+    if wl.name == "Li":
+        head = f"Li atom (hydrogenic Z=3, adaptive mesh p=4, tol_m {wl.meta.get('tol_m', 3e-7):g}): {wl.n} points, "
+    else:
+        head = f"{wl.name}, adaptive mesh p=4: {wl.n} points, "
+    return head + f"{wl.psi.shape[0]} orbitals + Hartree, degree {wl.degree}, theta {wl.theta}, leaf {wl.leaf_size}"
 
-    threads = oracle.threads(nthreads if nthreads > 0 else len(os.sched_getaffinity(0)))
-    m = wl.mesh
-    ot = oracle.Tree(m.xyz, wl.leaf_size)
-    b, c, k = ot.lists(wl.theta, wl.degree)
-    P = (wl.degree + 1) ** 3
-    size = ot.end - ot.begin
-    per_batch = {}
-    for bb, cc, kk in zip(b, c, k):
-        per_batch[bb] = per_batch.get(bb, 0) + (P if kk == 1 else int(size[cc]))
-    leaves = np.array(ot.leaves)
-    rng = np.random.default_rng(seed)
-    rng.shuffle(leaves)
-    fields = [(0, wl.k[o], wl.f[o]) for o in range(wl.psi.shape[0])] + [(1, wl.alpha, wl.rho)]
-    nf = len(fields)
-    t_ant = 0.0
-    for kern, par, f in fields:
-        ts = time.time()
-        ot.treecode_batches(wl.theta, wl.degree, kern, par, f, m.w, [])
-        t_ant += time.time() - ts
-    # size the sample from one probe batch
-    ts = time.time()
-    kern, par, f = fields[0]
-    ot.treecode_batches(wl.theta, wl.degree, kern, par, f, m.w, leaves[:1])
-    t_probe = max(time.time() - ts - t_ant / nf, 1e-3)
-    nb = int(max(1, min(len(leaves), (budget_s - 2 * t_ant) / (nf * t_probe))))
-    pick = leaves[:nb]
-    t_b = 0.0
-    for kern, par, f in fields:
-        ts = time.time()
-        ot.treecode_batches(wl.theta, wl.degree, kern, par, f, m.w, pick)
-        t_b += time.time() - ts
-    t_b -= t_ant
-    inter = sum(per_batch[x] * int(size[x]) for x in pick) * nf
-    share = nb / len(leaves)
-    desc = (f"{nb} of {len(leaves)} target batches x {nf} fields of this workload: {t_b:.2f} s of batch work + "
-            f"{share:.3f} x {t_ant:.2f} s whole-tree anterpolation")
-    return inter / (t_b + share * t_ant), threads, desc, t_b + t_ant
+
+def nucleus_batches(ot, xyz, nuclei, count=50):
+    """Leaves holding the `count` mesh points nearest each nucleus: where the
+    singularity subtraction cancels the most (f_i/k^2 >> |u_i|)."""
+    leaf_of = np.empty(xyz.shape[1], dtype=np.int64)
+    for c in ot.leaves:
+        leaf_of[ot.points(c)] = c
+    out = set()
+    for R in nuclei:
+        r = np.sqrt(((xyz - np.asarray(R, float)[:, None]) ** 2).sum(0))
+        out.update(int(c) for c in leaf_of[np.argsort(r)[:count]])
+    return sorted(out)
+
+
+class OracleSample:
+    """The float64 oracle treecode (as it stands, OpenMP over batches) on a
+    bounded sample of a workload's target batches, all fields: the sample
+    holds at least 2 batches per thread (so the dynamic batch schedule keeps
+    every core busy) and always the batches that meet at the nuclei.  The
+    oracle anterpolates every cluster on each call; that cost is timed once
+    on its own (a call with no batch) and charged to a sample in proportion
+    to its share of the batches, as a full run would amortise it."""
+
+    def __init__(self, wl, nthreads=0, nuclei=((0.0, 0.0, 0.0),)):
+        import oracle
+
+        self.oracle = oracle
+        self.wl = wl
+        self.threads = oracle.threads(nthreads if nthreads > 0 else len(os.sched_getaffinity(0)))
+        m = wl.mesh
+        self.ot = ot = oracle.Tree(m.xyz, wl.leaf_size)
+        b, c, k = ot.lists(wl.theta, wl.degree)
+        P = (wl.degree + 1) ** 3
+        self.size = ot.end - ot.begin
+        self.per_batch = {}
+        for bb, cc, kk in zip(b, c, k):
+            self.per_batch[bb] = self.per_batch.get(bb, 0) + (P if kk == 1 else int(self.size[cc]))
+        self.leaves = np.array(ot.leaves)
+        self.nuc = nucleus_batches(ot, m.xyz, nuclei)
+        self.fields = [(0, wl.k[o], wl.f[o]) for o in range(wl.psi.shape[0])] + [(1, wl.alpha, wl.rho)]
+        self.t_ant = 0.0
+        for kern, par, f in self.fields:
+            ts = time.time()
+            ot.treecode_batches(wl.theta, wl.degree, kern, par, f, m.w, [])
+            self.t_ant += time.time() - ts
+
+    def run(self, nbatch, seed=0, with_nucleus=True):
+        """Time the sample; returns (interactions/s, description, the oracle's
+        results per field restricted to the sample's targets, the targets,
+        the nucleus targets)."""
+        wl, ot = self.wl, self.ot
+        rng = np.random.default_rng(seed)
+        nuc = list(self.nuc) if with_nucleus else []
+        rest = np.array([c for c in self.leaves if c not in set(nuc)])
+        rng.shuffle(rest)
+        nb = int(min(len(self.leaves), max(nbatch, len(nuc) + 1)))
+        pick = np.array(nuc + list(rest[:nb - len(nuc)]))
+        t_b, outs = 0.0, []
+        for kern, par, f in self.fields:
+            ts = time.time()
+            outs.append(ot.treecode_batches(wl.theta, wl.degree, kern, par, f, wl.mesh.w, pick))
+            t_b += time.time() - ts
+        nf = len(self.fields)
+        t_b -= self.t_ant  # every call re-anterpolated the whole tree; charged below by share
+        inter = sum(self.per_batch[x] * int(self.size[x]) for x in pick) * nf
+        share = len(pick) / len(self.leaves)
+        desc = (f"{len(pick)} of {len(self.leaves)} target batches ({len(nuc)} at the nucleus, the rest "
+                f"seeded) x {nf} fields of this workload on {self.threads} threads: {t_b:.2f} s of batch work + "
+                f"{share:.3f} x {self.t_ant:.2f} s whole-tree anterpolation")
+        pts = np.concatenate([ot.points(c) for c in pick])
+        nuc_pts = np.concatenate([ot.points(c) for c in nuc]) if nuc else np.zeros(0, dtype=np.int64)
+        return inter / (t_b + share * self.t_ant), desc, outs, pts, nuc_pts
+
+
+def rel_err_vs_oracle(gpu_fields, outs, w, pts, nuc_pts):
+    """Relative L2 error of the GPU's fields against the oracle treecode at
+    the same (n, theta), on the sample's targets: unweighted (over mesh
+    points) and quadrature-weighted, for the nucleus batches and for the
+    other sampled batches."""
+    res = {}
+    other = np.setdiff1d(pts, nuc_pts)
+    names = [f"psi{o}" for o in range(len(outs) - 1)] + ["hartree"]
+    for name, g, ref in zip(names, gpu_fields, outs):
+        row = {}
+        for label, idx in (("nucleus", nuc_pts), ("other", other)):
+            d = g[idx] - ref[idx]
+            row[label] = {"plain": float(np.linalg.norm(d) / np.linalg.norm(ref[idx])),
+                          "weighted": float(np.sqrt(np.sum(d * d * w[idx]) / np.sum(ref[idx] ** 2 * w[idx])))}
+        res[name] = row
+    return res
 
 
 def run_reference(args):
     rank, world, local = dist_info()
     if rank != 0:
         return
-    wl = make_workload(0)
-    rates = []
-    desc = ""
+    wl = make_workload(1)
+    smp = OracleSample(wl)
+    rates, desc = [], ""
     for i in range(args.warmup + args.steps):
-        rate, threads, desc, _ = cpu_oracle_rate(wl, budget_s=8.0, seed=i)
+        rate, desc, *_ = smp.run(2 * smp.threads, seed=i)
         if i >= args.warmup:
             rates.append(rate)
     v = float(np.mean(rates))
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"Li atom, {wl.n} mesh points, 2 orbitals + Hartree, degree 8, theta 0.7, "
-                                  "leaf 2000", "model": "oracle treecode (float64 CPU)"},
-           "cpu_baseline": {"kind": "oracle", "value": v, "unit": UNIT, "cores": threads, "sample": desc},
+           "config": {"workload": workload_name(wl), "model": "oracle treecode (float64 CPU)"},
+           "cpu_baseline": {"kind": "oracle", "value": v, "unit": UNIT, "cores": smp.threads, "sample": desc},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -575,30 +648,48 @@ def main():
     h2d = 8 * n * (3 + 1 + 1 + 1 + nw)
     d2h = 8 * n * (nw + 1)
 
-    # ---- plain FP64 form: one orbital per launch, same tree, no graph
+    # ---- plain FP64 form: one orbital per launch, same tree, no graph.  One
+    # warm-up and three timed Green iterations on a tree built once, beside
+    # the FP32C eager Green iteration timed the same way.
     plain = None
     if not args.no_plain and rank == 0 and lithium:
+        def time_steps(prm, count, warm):
+            hh = T.tagi_tree_build(xyz, w, prm)
+            ts, res = [], None
+            for i in range(warm + count):
+                pb = psi0.clone()
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = T.tagi_green_step(hh, veff, wl.vshift, pb, wl.eps, rho=rho, vh=vh)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= warm:
+                    ts.append(e0.elapsed_time(e1))
+                res = (pb, r)
+            T.tagi_tree_destroy(hh)
+            return ts, res
         pp = T.make_params(theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size, prec=T.TAGI_FP64)
-        psi64 = psi0.clone()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h64 = T.tagi_tree_build(xyz, w, pp)
-        eps64, res64, eh64 = T.tagi_green_step(h64, veff, wl.vshift, psi64, wl.eps, rho=rho, vh=vh)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        T.tagi_tree_destroy(h64)
-        plain_ms = e0.elapsed_time(e1)
-        # accuracy of the FP32C step against the FP64 plain form on the GPU
-        psi32 = psi0.clone()
-        h = T.tagi_tree_build(xyz, w, params)
-        eps32, res32, eh32 = T.tagi_green_step(h, veff, wl.vshift, psi32, wl.eps, rho=rho, vh=vh)
-        T.tagi_tree_destroy(h)
+        t64, (psi64, (eps64, _, eh64)) = time_steps(pp, 3, 1)
+        t32, (psi32, (eps32, _, eh32)) = time_steps(params, 10, 3)
         a, b = psi32.cpu().numpy(), psi64.cpu().numpy()
         rel = [float(np.linalg.norm(a[o] - b[o]) / np.linalg.norm(b[o])) for o in range(nw)]
-        plain = {"s_per_green_iteration_fp64_plain": plain_ms * 1e-3, "speedup_vs_plain": plain_ms / ms,
+        p_ms, f_ms = float(np.median(t64)), float(np.median(t32))
+        plain = {"s_per_green_iteration_fp64_plain": p_ms * 1e-3, "plain_times_ms": t64,
+                 "s_per_green_iteration_fp32c_eager": f_ms * 1e-3,
+                 "speedup_vs_plain": p_ms / f_ms,
+                 "speedup_vs_plain_graph": p_ms / graph["ms_per_green_iteration"] if graph else None,
+                 "statistic": "median of 3 plain (after 1 warm-up) and of 10 FP32C (after 3) Green iterations "
+                              "on a tree built once, CUDA events, L2 flushed before each",
                  "fp32c_vs_fp64_psi_rel_l2": rel, "fp32c_vs_fp64_eps_abs": [float(x) for x in np.abs(eps32 - eps64)],
                  "fp32c_vs_fp64_eh_abs": abs(eh32 - eh64)}
+        if scf is not None and "gi_steps" in scf:
+            gi = float(np.mean(scf["gi_steps"]))
+            plain["s_per_scf_step_fp64_plain_estimate"] = gi * p_ms * 1e-3
+            plain["scf_estimate_note"] = (f"estimate, not measured: {gi:.1f} Green iterations per SCF step (the "
+                                          "FP32C SCF leg) x the measured plain s per Green iteration")
+            plain["speedup_vs_plain_per_scf_step_estimate"] = gi * p_ms * 1e-3 / scf["s_per_scf_step"]
 
     if rank != 0:
         return
@@ -607,20 +698,31 @@ def main():
     k_ms, k_cnt = prof["interact"]
     k_ms_per_step = k_ms / max(1, args.steps)
     clk_mhz = clk.get("sm_mhz") or 1900.0
-    achieved, peak, bounds = roofline(info, nw, True, k_ms_per_step, clk_mhz, sms)
-    cpu = None
+    rates = T.tagi_unit_rates()
+    achieved, peak, bounds = roofline(info, nw, True, k_ms_per_step, clk_mhz, sms, xu_rate=rates["ex2"])
+    cpu, rel_err = None, None
     if not args.no_cpu and lithium:
-        rate, threads, desc, _ = cpu_oracle_rate(wl, budget_s=20.0)
-        rate1, _, desc1, _ = cpu_oracle_rate(wl, budget_s=6.0, seed=1, nthreads=1)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+        # the fields of the step's convolutions on the GPU, for the error
+        # against the oracle on the oracle's own sample
+        hh = T.tagi_tree_build(xyz, w, params)
+        ug = torch.empty((nw, n), dtype=torch.float64, device=dev)
+        T.tagi_fields_conv(hh, torch.tensor(wl.f, device=dev), list(wl.k), ug, rho=rho, vh=vh)
+        torch.cuda.synchronize()
+        gpu_fields = list(ug.cpu().numpy()) + [vh.cpu().numpy()]
+        T.tagi_tree_destroy(hh)
+        smp = OracleSample(wl)
+        rate, desc, outs, pts, nuc_pts = smp.run(2 * smp.threads, seed=0)
+        rel_err = rel_err_vs_oracle(gpu_fields, outs, wl.mesh.w, pts, nuc_pts)
+        smp1 = OracleSample(wl, nthreads=1)
+        rate1, desc1, *_ = smp1.run(2, seed=1, with_nucleus=False)
+        smp.oracle.threads(smp.threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": smp.threads, "kind": "oracle", "sample": desc,
                "value_1_core": rate1, "sample_1_core": desc1}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
-        "config": {"workload": (f"Li atom (hydrogenic Z=3, adaptive mesh p=4, tol_m 3e-7): {n} points, "
-                                if WORKLOAD == "li" else f"{wl.name}, adaptive mesh p=4: {n} points, ") +
-                               f"{nw} orbitals + Hartree, degree {wl.degree}, theta {wl.theta}, leaf {wl.leaf_size}",
+        "config": {"workload": workload_name(wl),
                    "step": "tree+lists+items, fields, anterpolation, near/far kernel, SS epilogue, "
                            "eps update, MGS, residuals, E_H",
                    "interactions_per_step": inter, "near_pairs": info["near_pairs"], "far_pairs": info["far_pairs"],
@@ -631,10 +733,12 @@ def main():
                      "frac": achieved / peak, "traffic": kernel_traffic() if WORKLOAD == "li" else None,
                      "kernel": "k_interact32 (near/far)", **bounds,
                      "ncu_small_case_pct": kernel_pipes() if lithium else None,
+                     "unit_rates_per_sm_clk": rates,
                      "peak_model": f"min(issue: {sms} SMs x 128 instr/clk, MUFU: {sms} SMs x "
-                                   f"{XU_EX2_PER_SM_CLK} ex2/clk) x {clk_mhz:.0f} MHz (measured clock) over the "
-                                   "per-interaction counts; peak of measured unit rates, not MEASURED_PEAKS.json "
+                                   f"{rates['ex2']:.1f} ex2/clk measured live by tagi_unit_rates) x {clk_mhz:.0f} MHz "
+                                   "(measured clock) over the per-interaction counts; not MEASURED_PEAKS.json "
                                    "(HBM and bf16 tensor peaks do not bound this kernel)"},
+        "rel_err_vs_oracle": rel_err,
         "clocks": clk,
         "e2e": {"value": inter_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "s_per_step": e2e_s},

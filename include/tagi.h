@@ -132,7 +132,15 @@ tagi_status tagi_tree_lists(const tagi_tree* tree, int64_t cap, int32_t* batch, 
  * cluster's Chebyshev points of the second kind.
  *   q [dev] nq*n float64 charges in the caller's order; nq >= 1.
  *   qh [dev] n_clusters*nq*(degree+1)^3 float64, caller-owned.
- * Computed in float64 whatever the tree's precision. */
+ * The arithmetic is the tree's, as its Green steps anterpolate their fields:
+ *   TAGI_FP64: float64 throughout;
+ *   TAGI_FP32C: charges rounded to float32, the basis evaluated in float64 on
+ *     the float32-rounded nodes (where that form's proxies sit) and rounded to
+ *     float32, products on the tensor cores in split precision (3xTF32) with
+ *     float32 accumulation over 64 points, partial sums added in float64.
+ *     Relative error about 1e-7 of a cluster's largest weight.
+ * Synchronises the stream.  TAGI_ERR_TIMEOUT if a bounded wait of the
+ * tensor-core kernel gave up. */
 tagi_status tagi_anterpolate(tagi_tree* tree, const double* q, int nq, double* qh, void* stream);
 
 /* Yukawa convolution for nf fields with their own decay rates:
@@ -209,13 +217,23 @@ tagi_status tagi_fp32_bias(double* beta_yukawa, double* beta_gauss, void* stream
 tagi_status tagi_profile_enable(int on);
 tagi_status tagi_profile_read(int group, double* ms, int64_t* count);
 
+/* Measured throughput of the units that bound the near/far kernel, in thread
+ * operations per SM per SM clock (median over SMs; one CTA of 1024 threads
+ * per SM runs independent operations in a loop and reads clock64 at both
+ * ends):  rates[0] FP32 FMA (fma.rn.f32), rates[1] FP32 FMA issued as packed
+ * f32x2 pairs (counted per FMA), rates[2] ex2.approx.ftz.f32, rates[3]
+ * rsqrt.approx.ftz.f32, rates[4] FP64 FMA.  rates [host] n_rates >= 5.
+ * Takes a few milliseconds; synchronises the stream. */
+tagi_status tagi_unit_rates(double* rates, int n_rates, void* stream);
+
 /* Direct-sum Yukawa convolution that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc -- code recording a CUDA graph, host frameworks that
- * own every device byte through their own memory pool and forbid hidden
- * allocations, latency-critical loops that cannot take an allocation's
- * implicit synchronisation.  It computes, in float64, the same sum as
- * tagi_yukawa_conv with singularity subtraction on a tree with theta = 0:
+ * cannot let a library call cudaMalloc -- host frameworks that hand out every
+ * device byte from their own memory pool (a second allocator would fragment
+ * it or exceed its budget), and latency-critical loops in which an
+ * allocation's implicit device synchronisation would stall other streams.
+ * It computes, in float64, the same sum as tagi_yukawa_conv with singularity
+ * subtraction on a tree with theta = 0:
  *   u[o][i] = sum_{j, r_ij != 0} G_{k_o}(r_ij) (f[o][j] - f[o][i]) w_j + f[o][i] / k_o^2,
  * G_k(r) = exp(-k r) / (4 pi r), over all n points (O(n^2) work).
  *   xyz [dev] 3*n float64 (structure of arrays), w [dev] n, f [dev] nf*n,
@@ -225,9 +243,12 @@ tagi_status tagi_profile_read(int group, double* ms, int64_t* count);
  * n * nf > 1048576 are rejected with TAGI_ERR_INVALID_ARG.  All calls share
  * that array and it keeps the last call's contents: two calls whose work
  * overlaps on the GPU (different streams, or different host threads on the
- * same device) race and give wrong results; serialise them.  Each call writes
- * every scratch value it reads, so stale contents are never used.
- * The first call on each device looks up the array's device address
+ * same device) race and give wrong results.  The caller's stream must be the
+ * only one using this entry point on its device until the call's work has
+ * completed.  Each call writes every scratch value it reads, so stale
+ * contents are never used.
+ * Set-up: the first call on each device (and after a cudaDeviceReset, the
+ * first call in the new context) looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Enqueued on `stream`, asynchronous. */
 tagi_status tagi_yukawa_direct_noalloc(const double* xyz, const double* w, const double* f, const double* k,

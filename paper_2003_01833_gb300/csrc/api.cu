@@ -148,18 +148,26 @@ RateSrc host_rates(const Tree& T, int nf)
     return R;
 }
 
+// errflag[0]: argument checks of the current call (cleared by every call);
+// errflag[1]: sticky, set when a bounded device wait gave up (reported by the
+// next call that reads the flags).
 void clear_err(Tree& T)
 {
-    T.errflag.ensure(16);
-    TAGI_CUDA(cudaMemsetAsync(T.errflag.p, 0, 4, T.stream));
+    if (!T.errflag.p) {
+        T.errflag.ensure(16);
+        TAGI_CUDA(cudaMemsetAsync(T.errflag.p, 0, 16, T.stream));
+    } else {
+        TAGI_CUDA(cudaMemsetAsync(T.errflag.p, 0, 4, T.stream));
+    }
 }
 
 int read_err(Tree& T)
 {
-    int h = 0;
-    TAGI_CUDA(cudaMemcpyAsync(&h, T.errflag.p, 4, cudaMemcpyDeviceToHost, T.stream));
+    int h[2] = {0, 0};
+    TAGI_CUDA(cudaMemcpyAsync(h, T.errflag.p, 8, cudaMemcpyDeviceToHost, T.stream));
     TAGI_CUDA(cudaStreamSynchronize(T.stream));
-    return h;
+    if (h[1]) throw Error(TAGI_ERR_TIMEOUT, "a bounded wait of the tensor-core anterpolation gave up");
+    return h[0];
 }
 
 namespace {
@@ -380,7 +388,13 @@ tagi_status tagi_anterpolate(tagi_tree* tree, const double* q, int nq, double* q
         TAGI_REQUIRE(nq >= 1, "nq must be >= 1");
         T->stream = (cudaStream_t)stream;
         AllocStream as(T->stream);
-        anterpolate_all_clusters64(*T, q, nq, qh);
+        if (T->prec == TAGI_FP32C) {
+            clear_err(*T);
+            anterpolate_all_clusters32(*T, q, nq, qh);
+            read_err(*T);
+        } else {
+            anterpolate_all_clusters64(*T, q, nq, qh);
+        }
     });
 }
 
@@ -655,10 +669,11 @@ tagi_status tagi_green_graph_check(tagi_green_graph* graph, void* stream)
         TAGI_REQUIRE(graph != nullptr, "graph is NULL");
         GreenGraph* G = reinterpret_cast<GreenGraph*>(graph);
         Tree* T = G->T;
-        int h = 0;
-        TAGI_CUDA(cudaMemcpyAsync(&h, T->errflag.p, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+        int h[2] = {0, 0};
+        TAGI_CUDA(cudaMemcpyAsync(h, T->errflag.p, 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
         TAGI_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-        TAGI_REQUIRE(h == 0, "eps + vshift became non-negative during a replay (Section 3.3)");
+        if (h[1]) throw Error(TAGI_ERR_TIMEOUT, "a bounded wait of the tensor-core anterpolation gave up");
+        TAGI_REQUIRE(h[0] == 0, "eps + vshift became non-negative during a replay (Section 3.3)");
     });
 }
 

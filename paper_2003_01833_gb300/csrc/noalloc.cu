@@ -1,18 +1,19 @@
 // An entry point that allocates no device memory: the float64 direct-sum
-// Yukawa convolution with singularity subtraction, for callers that must not
-// (or cannot) call cudaMalloc -- code running while a CUDA graph is being
-// captured on a stream the allocator may not touch, host frameworks that own
-// every device byte through their own pool and forbid hidden allocations, or
-// latency-critical loops where an allocation's implicit synchronisation is
-// not acceptable.  The caller passes inputs and outputs; the only other
-// device memory used is one file-scope scratch array of fixed size that the
-// library's module carries on every GPU that loads it, until process exit.
+// Yukawa convolution with singularity subtraction, for callers that cannot
+// let a library call cudaMalloc -- host frameworks that hand out every
+// device byte from their own pool (a second allocator would fragment it or
+// exceed its budget), and latency-critical loops in which an allocation's
+// implicit device synchronisation would stall other streams.  The caller
+// passes inputs and outputs; the only other device memory used is one
+// file-scope scratch array of fixed size that the library's module carries on
+// every GPU that loads it, until process exit.
 //
 // It is a variant of the float64 near/far interaction kernel (k_interact64)
 // that needs no tree: every target sums over every source (the theta = 0 case
 // of the treecode, i.e. the direct sum), with the source range split into a
 // few slices whose partial sums go to the scratch array and are reduced in a
 // fixed order.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -93,9 +94,16 @@ __global__ void k_direct_noalloc_reduce(const double* __restrict__ f, NaRates ra
     u[e] = S / (4.0 * 3.14159265358979323846) + f[e] / (k * k);
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up at set-up: once per device
+// and CUDA context (the first call with that device current).  Keying on the
+// context means that a call after cudaDeviceReset, which unloads the module
+// and may load it again elsewhere, repeats the set-up instead of using the
+// old address.
+using CtxGetCurrent = CUresult (*)(CUcontext*);
 std::mutex g_na_mu;
 void* g_na_ptr[kNaMaxDevices] = {nullptr};
+CUcontext g_na_ctx[kNaMaxDevices] = {nullptr};
+CtxGetCurrent g_ctx_get = nullptr;
 
 double* scratch_address()
 {
@@ -103,10 +111,23 @@ double* scratch_address()
     TAGI_CUDA(cudaGetDevice(&dev));
     TAGI_REQUIRE(dev >= 0 && dev < kNaMaxDevices, "device ordinal out of range for the no-alloc scratch table");
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    if (!g_ctx_get) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        TAGI_CUDA(cudaGetDriverEntryPoint("cuCtxGetCurrent", &fn, cudaEnableDefault, &q));
+        TAGI_REQUIRE(fn != nullptr && q == cudaDriverEntryPointSuccess, "cuCtxGetCurrent is not available");
+        g_ctx_get = reinterpret_cast<CtxGetCurrent>(fn);
+    }
+    // no context may be bound to this host thread yet; the set-up below binds
+    // the device's primary context (cudaGetSymbolAddress initialises it)
+    CUcontext ctx = nullptr;
+    if (g_ctx_get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    if (!ctx || !g_na_ptr[dev] || g_na_ctx[dev] != ctx) {
         void* p = nullptr;
         TAGI_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        TAGI_REQUIRE(g_ctx_get(&ctx) == CUDA_SUCCESS && ctx != nullptr, "no current CUDA context");
         g_na_ptr[dev] = p;
+        g_na_ctx[dev] = ctx;
     }
     return static_cast<double*>(g_na_ptr[dev]);
 }

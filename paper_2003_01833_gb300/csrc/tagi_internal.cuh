@@ -193,6 +193,7 @@ struct Tree {
     DevBuf part;        // double partial sums
     DevBuf antpart;     // double anterpolation partials
     DevBuf antL;        // FP32C: float32 basis rows of every anterpolation point (anterp.cu)
+    DevBuf qtiles;      // FP32C: charge tiles of the tensor-core anterpolation (anterp.cu)
     DevBuf scratch;     // general scratch (reductions)
     DevBuf rates32;     // float [kMaxCallFields] exponent factors of the current call
     DevBuf rates64;     // double [kMaxCallFields] k or alpha as applied by the kernels
@@ -211,6 +212,7 @@ void anterpolate_weights(Tree& T);  // w^ for every approximated cluster (FP32C 
 void anterpolate_fields32(Tree& T, int nf);  // q^ rows [0, nf) of T.fa from T.qant
 void anterpolate_fields64(Tree& T, int nf);
 void anterpolate_all_clusters64(Tree& T, const double* q, int nq, double* qh);
+void anterpolate_all_clusters32(Tree& T, const double* q, int nq, double* qh);  // FP32C form (tensor cores)
 // interact.cu
 // kinds[o]: 0 = Yukawa with kval[o], 1 = Coulomb/Hartree
 void interact32(Tree& T, int nf, const int* kinds, const float* kyd, double* part);

@@ -126,6 +126,8 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.tagi_yukawa_direct_noalloc.argtypes = [_vp, _vp, _vp, _D, ctypes.c_int, ctypes.c_int64, _vp, _vp]
         L.tagi_yukawa_direct_noalloc.restype = ctypes.c_int
+        L.tagi_unit_rates.argtypes = [_D, ctypes.c_int, _vp]
+        L.tagi_unit_rates.restype = ctypes.c_int
         L.tagi_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_int64, ctypes.POINTER(_vp)]
         L.tagi_mlp_get_params.argtypes = [_vp, _D, ctypes.c_int64, _vp]
         L.tagi_mlp_features.argtypes = [_vp, ctypes.c_int64, _D, ctypes.c_int, _vp, _vp]
@@ -413,6 +415,18 @@ def tagi_fp32_bias(stream=None):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().tagi_fp32_bias(ctypes.byref(a), ctypes.byref(b), _stream(stream)))
     return a.value, b.value
+
+
+UNIT_RATE_NAMES = ("ffma", "ffma_packed", "ex2", "rsqrt", "dfma")
+
+
+def tagi_unit_rates(stream=None):
+    """Measured thread operations per SM per SM clock of the units that bound
+    the near/far kernel: FP32 FMA (scalar, packed f32x2), ex2.approx,
+    rsqrt.approx, FP64 FMA (see include/tagi.h)."""
+    out = np.zeros(5)
+    _check(lib().tagi_unit_rates(out.ctypes.data_as(_D), 5, _stream(stream)))
+    return dict(zip(UNIT_RATE_NAMES, (float(x) for x in out)))
 
 
 def tagi_yukawa_direct_noalloc(xyz, w, f, k, u, stream=None):

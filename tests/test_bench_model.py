@@ -47,3 +47,41 @@ def test_roofline_groups(bench):
     # 21 Yukawa + H: 8, 8 and 5 + H
     i5, _ = bench.kernel_work(INFO, 5, True)
     assert work(21, True) == pytest.approx((2 * i8 + i5) / (300 * 22))
+
+
+def test_oracle_sample_covers_nucleus_and_every_thread(bench):
+    """The CPU legs time the oracle on at least 2 batches per thread and
+    always on the batches that meet at the nucleus; the sample reports the
+    oracle's fields there, which the error leg compares with the GPU."""
+    import numpy as np
+
+    from paper_2003_01833_gb300 import workloads as W
+
+    wl = W.hydrogen_adaptive()
+    wl.degree, wl.leaf_size = 4, 500
+    smp = bench.OracleSample(wl, nthreads=2)
+    assert smp.threads == 2 and len(smp.nuc) >= 1
+    rate, desc, outs, pts, nuc_pts = smp.run(2 * smp.threads, seed=0)
+    assert rate > 0 and len(outs) == 2
+    assert set(nuc_pts) <= set(pts)
+    nb = sum(1 for c in smp.leaves if set(smp.ot.points(c)) <= set(pts))
+    assert nb >= max(2 * smp.threads, len(smp.nuc) + 1)
+    # the oracle's own fields against themselves: zero error; a 1e-6 relative
+    # perturbation of the nucleus targets shows up there and not elsewhere
+    e0 = bench.rel_err_vs_oracle(outs, outs, wl.mesh.w, pts, nuc_pts)
+    assert all(v[s][k] == 0.0 for v in e0.values() for s in ("nucleus", "other") for k in ("plain", "weighted"))
+    g = [o.copy() for o in outs]
+    for o in g:
+        o[nuc_pts] *= 1 + 1e-6
+    e1 = bench.rel_err_vs_oracle(g, outs, wl.mesh.w, pts, nuc_pts)
+    for v in e1.values():
+        assert abs(v["nucleus"]["plain"] - 1e-6) < 1e-9 and v["other"]["plain"] == 0.0
+    np.testing.assert_allclose(e1["hartree"]["nucleus"]["weighted"], 1e-6, rtol=1e-3)
+
+
+def test_workload_names_match_between_arms(bench):
+    from paper_2003_01833_gb300 import workloads as W
+
+    wl = W.hydrogen_1s()
+    assert bench.workload_name(wl) == bench.workload_name(wl)
+    assert f"{wl.n} points" in bench.workload_name(wl)

@@ -151,6 +151,45 @@ def test_anterpolation_fp64_matches_oracle(T):
             np.testing.assert_allclose(qh[c], ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("degree,nq,leaf", [(1, 1, 700), (5, 2, 400), (8, 3, 3000), (8, 5, 1500), (6, 8, 900),
+                                             (8, 8, 2500), (9, 8, 5000)])
+def test_anterpolation_fp32c_tensor_cores_matches_oracle(T, degree, nq, leaf):
+    """The FP32C anterpolation (3xTF32 tcgen05 products, the path a Green
+    step runs) against the float64 oracle on every cluster: column groups of
+    N = 16..80 tensor columns, clusters of more than 2048 points (several
+    work items) and sizes that are not multiples of the 32-point tile."""
+    xyz, w, f = case_cube(12007, seed=5 + nq)
+    rng = np.random.default_rng(degree)
+    q = np.stack([w * (1.0 + 0.5 * np.sin(2.0 * xyz[0] + o) * np.cos(1.3 * xyz[2] - o) + 0.1 * rng.normal(size=w.size))
+                  for o in range(nq)])
+    with build(T, xyz, w, theta=0.7, degree=degree, leaf_size=leaf, prec=T.TAGI_FP32C) as tr:
+        ex = T.tagi_tree_export(tr.handle)
+        nc = len(ex["begin"])
+        sizes = np.asarray(ex["end"]) - np.asarray(ex["begin"])
+        assert sizes.max() > 2048 and np.any(sizes % 32)
+        P = (degree + 1) ** 3
+        qh = torch.empty((nc, nq, P), dtype=torch.float64, device="cuda")
+        T.tagi_anterpolate(tr.handle, dev(q), qh)
+        qh = qh.cpu().numpy()
+        ot = oracle.Tree(xyz, leaf)
+        ok_ = {ot.key(c): c for c in range(ot.nc)}
+        worst, signed = 0.0, []
+        for c, key in gpu_keys(ex).items():
+            ref = ot.anterpolate(ok_[key], degree, q)
+            scale = np.abs(ref).max(axis=1, keepdims=True)
+            worst = max(worst, float((np.abs(qh[c] - ref) / scale).max()))
+            big = np.abs(ref) > 0.1 * scale
+            signed.append(((qh[c] - ref) / np.abs(ref))[big])
+        # systematic shrinkage of the weights: the tensor cores' float32
+        # accumulation rounds toward zero, which leaves a mean relative error
+        # of -4e-8 to -1.5e-7 (measured); it stays an order of magnitude
+        # below the 1e-6 error bar of the method
+        bias = float(np.mean(np.concatenate(signed)))
+        print(f"degree {degree}, {nq} columns: worst {worst:.2e}, mean signed relative error {bias:.2e}")
+        assert worst < 2e-6, worst
+        assert abs(bias) < 2e-7, bias
+
+
 # ------------------------------------------------------------------ FP64 plain form
 @pytest.mark.parametrize("theta,degree", [(0.7, 6), (0.5, 4), (0.0, 3)])
 def test_yukawa_fp64_matches_oracle(T, theta, degree):
