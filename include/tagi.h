@@ -187,6 +187,53 @@ tagi_status tagi_green_step(tagi_tree* tree, const double* veff, double vshift, 
                             double* eps, int nw, const double* rho, double* vh, double* resid,
                             double* eh, void* stream);
 
+/* ------------------------------------------------------------------------
+ * The Green step split over target batches, one process per GPU.  Batches
+ * are independent once the tree, lists and proxy weights exist (Section 5.5;
+ * the paper's multi-GPU runs share the batches out, Section 5.6).  Each
+ * process builds the same tree from the same inputs (the build is
+ * deterministic), forms and anterpolates every field itself, and computes
+ * the convolutions for its own batches only; each target's sums are then
+ * bit for bit those of the whole step.  The processes exchange the results
+ * (every target is written by exactly one of them) and apply
+ * tagi_green_reduce to the full fields.
+ * ------------------------------------------------------------------------ */
+
+/* Per batch, in the tree's fixed batch order (0 .. n_leaves-1): size [host]
+ * n_leaves targets, cost [host] n_leaves interactions per field
+ * (|B| x (near sources + far proxies)).  Either may be NULL.  Synchronises
+ * the tree's stream. */
+tagi_status tagi_tree_batches(const tagi_tree* tree, int32_t* size, int64_t* cost);
+
+/* tagi_fields_conv for the targets of the listed batches only: u and vh are
+ * written at those targets and left untouched elsewhere.
+ *   batches [host] nb distinct batch indices (0 <= b < n_leaves); nb = 0 is
+ *   a no-op.  Synchronises the stream. */
+tagi_status tagi_fields_conv_batches(tagi_tree* tree, const double* f, const double* k, int nf_y, const double* rho,
+                                     double* u, double* vh, const int32_t* batches, int nb, void* stream);
+
+/* The convolutions of tagi_green_step for the targets of the listed batches:
+ * f_o = (veff + vshift) psi_o, k_o = sqrt(-2 (eps_o + vshift)) (Eq.
+ * gauge-shift); u[o] = Yukawa_{k_o}[f_o] (so psi~ = -2 u, Eq. Yukawa) and,
+ * with rho, vh = the Hartree potential, both written at the batches' targets
+ * only.  veff [dev] n, psi [dev] nw*n (not modified), eps [host] nw
+ * unshifted; u [dev] nw*n, vh [dev] n.  Errors: TAGI_ERR_INVALID_ARG when
+ * eps_o + vshift >= 0.  Synchronises the stream. */
+tagi_status tagi_green_conv_batches(tagi_tree* tree, const double* veff, double vshift, const double* psi,
+                                    const double* eps, int nw, const double* rho, double* u, double* vh,
+                                    const int32_t* batches, int nb, void* stream);
+
+/* Algorithm 2 lines 4-6 of tagi_green_step given the full convolution
+ * results u (nw*n, as tagi_green_conv_batches writes them; not modified):
+ * the gradient-free eigenvalue update, modified Gram-Schmidt in index
+ * order, normalisation, residuals, and with rho E_H = 1/2 sum vh rho w.
+ * psi [dev] in: the orbitals the convolutions used, out: the new ones;
+ * eps [host] in/out; resid [host] nw or NULL; eh [host] or NULL.
+ * Synchronises the stream. */
+tagi_status tagi_green_reduce(tagi_tree* tree, const double* veff, double vshift, double* psi, double* eps, int nw,
+                              const double* u, const double* rho, const double* vh, double* resid, double* eh,
+                              void* stream);
+
 /* Diagnostics (no counterpart in the paper).
  * tagi_kernel_launches: number of CUDA kernels this library has launched in
  * this process so far (monotonic; differences bracket a region of interest).

@@ -128,6 +128,15 @@ def lib():
         L.tagi_yukawa_direct_noalloc.restype = ctypes.c_int
         L.tagi_unit_rates.argtypes = [_D, ctypes.c_int, _vp]
         L.tagi_unit_rates.restype = ctypes.c_int
+        L.tagi_tree_batches.argtypes = [_vp, _I32, _I64]
+        L.tagi_fields_conv_batches.argtypes = [_vp, _vp, _D, ctypes.c_int, _vp, _vp, _vp, _I32, ctypes.c_int, _vp]
+        L.tagi_green_conv_batches.argtypes = [_vp, _vp, ctypes.c_double, _vp, _D, ctypes.c_int, _vp, _vp, _vp,
+                                              _I32, ctypes.c_int, _vp]
+        L.tagi_green_reduce.argtypes = [_vp, _vp, ctypes.c_double, _vp, _D, ctypes.c_int, _vp, _vp, _vp, _D, _D,
+                                        _vp]
+        for name in ("tagi_tree_batches", "tagi_fields_conv_batches", "tagi_green_conv_batches",
+                     "tagi_green_reduce"):
+            getattr(L, name).restype = ctypes.c_int
         L.tagi_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_int64, ctypes.POINTER(_vp)]
         L.tagi_mlp_get_params.argtypes = [_vp, _D, ctypes.c_int64, _vp]
         L.tagi_mlp_features.argtypes = [_vp, ctypes.c_int64, _D, ctypes.c_int, _vp, _vp]
@@ -293,6 +302,72 @@ def tagi_fields_conv(tree, f, k, u, rho=None, vh=None, stream=None):
         raise ValueError("one decay rate per Yukawa field")
     _check(lib().tagi_fields_conv(tree, _dptr(f, "f"), ka.ctypes.data_as(_D), nf_y, _dptr(rho, "rho"),
                                   _dptr(u, "u"), _dptr(vh, "vh"), _stream(stream)))
+
+
+def tagi_tree_batches(tree):
+    """Per batch (the tree's batch order): (targets, interactions per field)
+    as NumPy int arrays."""
+    nb = tagi_tree_info(tree)["n_leaves"]
+    size = np.zeros(nb, dtype=np.int32)
+    cost = np.zeros(nb, dtype=np.int64)
+    _check(lib().tagi_tree_batches(tree, size.ctypes.data_as(_I32), cost.ctypes.data_as(_I64)))
+    return size, cost
+
+
+def _batch_list(batches):
+    b = np.ascontiguousarray(np.atleast_1d(np.asarray(batches, dtype=np.int64)), dtype=np.int32)
+    return b, (b.ctypes.data_as(_I32) if b.size else None)
+
+
+def tagi_fields_conv_batches(tree, f, k, u, batches, rho=None, vh=None, stream=None):
+    """tagi_fields_conv for the targets of the listed batches only."""
+    n = _tree_n(tree)
+    nf_y = 0 if f is None else (f.shape[0] if f.dim() == 2 else 1)
+    if (f is not None and (f.numel() != nf_y * n or u is None or u.numel() != nf_y * n)) or (
+            rho is not None and (rho.numel() != n or vh is None or vh.numel() != n)):
+        raise ValueError("f and u must be (nf_y, n); rho and vh must have n elements")
+    ka = np.ascontiguousarray(np.atleast_1d(k if k is not None else []), dtype=np.float64)
+    if ka.size != nf_y:
+        raise ValueError("one decay rate per Yukawa field")
+    b, bp = _batch_list(batches)
+    _check(lib().tagi_fields_conv_batches(tree, _dptr(f, "f"), ka.ctypes.data_as(_D), nf_y, _dptr(rho, "rho"),
+                                          _dptr(u, "u"), _dptr(vh, "vh"), bp, int(b.size), _stream(stream)))
+
+
+def tagi_green_conv_batches(tree, veff, vshift, psi, eps, u, batches, rho=None, vh=None, stream=None):
+    """The convolutions of a Green step for the targets of the listed batches:
+    u (nw, n) <- Yukawa_k[(veff + vshift) psi], vh <- Hartree[rho] there."""
+    nw = psi.shape[0] if psi.dim() == 2 else 1
+    n = _tree_n(tree)
+    if psi.numel() != nw * n or u.numel() != nw * n or veff.numel() != n or (
+            rho is not None and (rho.numel() != n or vh is None or vh.numel() != n)):
+        raise ValueError("psi and u must be (nw, n); veff, rho and vh must have n elements")
+    ea, ep = _hd(np.atleast_1d(eps).copy())
+    if ea.size != nw:
+        raise ValueError("one eigenvalue per orbital")
+    b, bp = _batch_list(batches)
+    _check(lib().tagi_green_conv_batches(tree, _dptr(veff, "veff"), float(vshift), _dptr(psi, "psi"), ep, nw,
+                                         _dptr(rho, "rho"), _dptr(u, "u"), _dptr(vh, "vh"), bp, int(b.size),
+                                         _stream(stream)))
+
+
+def tagi_green_reduce(tree, veff, vshift, psi, eps, u, rho=None, vh=None, stream=None):
+    """Algorithm 2 lines 4-6 given the full convolution results u; psi is
+    updated in place.  Returns (eps_new, resid, eh) like tagi_green_step."""
+    nw = psi.shape[0] if psi.dim() == 2 else 1
+    n = _tree_n(tree)
+    if psi.numel() != nw * n or u.numel() != nw * n or veff.numel() != n or (
+            rho is not None and (rho.numel() != n or vh is None or vh.numel() != n)):
+        raise ValueError("psi and u must be (nw, n); veff, rho and vh must have n elements")
+    ea, ep = _hd(np.atleast_1d(eps).copy())
+    if ea.size != nw:
+        raise ValueError("one eigenvalue per orbital")
+    res = np.zeros(nw)
+    eh = np.zeros(1)
+    _check(lib().tagi_green_reduce(tree, _dptr(veff, "veff"), float(vshift), _dptr(psi, "psi"), ep, nw,
+                                   _dptr(u, "u"), _dptr(rho, "rho"), _dptr(vh, "vh"), res.ctypes.data_as(_D),
+                                   eh.ctypes.data_as(_D) if rho is not None else None, _stream(stream)))
+    return ea, res, (float(eh[0]) if rho is not None else None)
 
 
 def tagi_green_step(tree, veff, vshift, psi, eps, rho=None, vh=None, stream=None):
