@@ -593,14 +593,78 @@ def h2_bond_lengths(seed: int = 5, count: int = 32, lo: float = 1.0, hi: float =
 def benzene(seed: int = 3, tol_m: float = 3e-8, p: int = 4, half_width: float = 20.0,
             n_orb: int = 21, uniform_levels: int = 3) -> Workload:
     """C6H6 in the z=0 plane at the paper's geometry (Section 6)."""
-    C = [(-0.682781, 2.548170), (0.682781, -2.548170), (2.548230, -0.682767), (-2.548230, 0.682767),
-         (1.86544, 1.86541), (-1.86544, -1.86541)]
-    H = [(-1.21247, 4.52502), (1.21247, -4.52502), (4.52548, -1.21333), (-4.52548, 1.21333),
-         (3.31252, 3.31351), (-3.31252, -3.31351)]
-    pos = np.array([[x, y, 0.0] for x, y in C + H])
+    pos = np.array([[x, y, 0.0] for x, y in BENZENE_C + BENZENE_H])
     mol = Molecule(["C"] * 6 + ["H"] * 6, pos)
     mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
     return _molecule_workload("C6H6", mol, mesh, seed, n_orb)
+
+
+BENZENE_C = [(-0.682781, 2.548170), (0.682781, -2.548170), (2.548230, -0.682767), (-2.548230, 0.682767),
+             (1.86544, 1.86541), (-1.86544, -1.86541)]
+BENZENE_H = [(-1.21247, 4.52502), (1.21247, -4.52502), (4.52548, -1.21333), (-4.52548, 1.21333),
+             (3.31252, 3.31351), (-3.31252, -3.31351)]
+
+
+def benzene_scf(tol_m: float = 3e-8, p: int = 4, half_width: float = 20.0, uniform_levels: int = 3) -> Workload:
+    """C6H6 for an SCF run from an aufbau-style start: 21 orbitals (N_e = 42,
+    every level doubly occupied), built from the Slater-screened atomic
+    orbitals and orthonormalised in this order:
+      6 carbon 1s;
+      6 C-C sigma bonds: the two sp2 hybrids (2s + sqrt(2) 2p)/sqrt(3) that
+        point along the bond, summed;
+      6 C-H sigma bonds: the carbon hybrid pointing at its hydrogen plus the
+        hydrogen 1s;
+      3 pi levels: the carbon 2p_z combinations of the lowest Hueckel levels
+        of the ring (all in phase, and weighted by the cosine and the sine
+        of each carbon's angle around the ring).
+    Eigenvalue guesses -9.9 (1s), -0.8 (C-C), -0.6 (C-H), -0.45 and -0.3
+    (pi) Ha; V_shift = -1.5 (c31).  The default tol_m = 3e-8 mesh has about
+    4.6M points; the paper's Table timings row used tol_m = 3e-6 (1,464,500
+    points)."""
+    pos = np.array([[x, y, 0.0] for x, y in BENZENE_C + BENZENE_H])
+    mol = Molecule(["C"] * 6 + ["H"] * 6, pos)
+    mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
+    pts = mesh.xyz.T
+    (_, _, z1), (_, _, z2), _ = _shells("C")
+    Cpos, Hpos = pos[:6], pos[6:]
+
+    def hybrid(i, target):
+        R = Cpos[i]
+        r = _dist(pts, R)
+        d = (target - R) / np.linalg.norm(target - R)
+        p_dir = radial_orbital("2p", z2, r) * ((pts - R) @ d) / np.maximum(r, 1e-300)
+        return (radial_orbital("2s", z2, r) + math.sqrt(2.0) * p_dir) / math.sqrt(3.0)
+
+    def pz(i):
+        R = Cpos[i]
+        r = _dist(pts, R)
+        return radial_orbital("2p", z2, r) * (pts[:, 2] - R[2]) / np.maximum(r, 1e-300)
+
+    basis = [radial_orbital("1s", z1, _dist(pts, R)) for R in Cpos]
+    pairs = [(i, j) for i in range(6) for j in range(i + 1, 6) if np.linalg.norm(Cpos[i] - Cpos[j]) < 3.0]
+    assert len(pairs) == 6
+    basis += [hybrid(i, Cpos[j]) + hybrid(j, Cpos[i]) for i, j in pairs]
+    for i in range(6):
+        h = int(np.argmin(np.linalg.norm(Hpos - Cpos[i], axis=1)))
+        basis.append(hybrid(i, Hpos[h]) + radial_orbital("1s", 1.0, _dist(pts, Hpos[h])))
+    ang = np.arctan2(Cpos[:, 1], Cpos[:, 0])
+    basis.append(sum(pz(i) for i in range(6)))
+    basis.append(sum(math.cos(ang[i]) * pz(i) for i in range(6)))
+    basis.append(sum(math.sin(ang[i]) * pz(i) for i in range(6)))
+    w = mesh.w
+    q = []
+    for v in basis:
+        v = v.copy()
+        for u in q:
+            v -= np.sum(v * u * w) * u
+        q.append(v / np.sqrt(np.sum(v * v * w)))
+    rho = density0(mol, pts)
+    vx = v_ext(mol, pts)
+    veff = vx + v_hartree0(mol, pts) + lda_xc(rho)[1]
+    eps = np.array([-9.9] * 6 + [-0.8] * 6 + [-0.6] * 6 + [-0.45, -0.3, -0.3])
+    return Workload(name="C6H6", mesh=mesh, veff=veff, psi=np.array(q), eps=eps, rho=rho, vshift=-1.5, theta=0.7,
+                    degree=8, leaf_size=2000, meta={"tol_m": tol_m, "start": "aufbau"}, vext=vx, n_elec=42.0,
+                    e_zz=nuclear_repulsion(mol))
 
 
 def _molecule_workload(name, mol, mesh, seed, n_orb):

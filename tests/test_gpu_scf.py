@@ -188,3 +188,52 @@ def test_lithium_scf_with_stored_outputs_reaches_the_papers_energy_closer(T):
     assert hist[-1][0] < 1e-4
     assert abs(hist[-1][1] - E_REF_LI) < 1e-3
     assert eps[0] < eps[1] < 0
+
+
+def test_benzene_scf_step_full_size(T):
+    """One SCF step of C6H6 on the 4.6M-point mesh (tol_m = 3e-8), 21
+    orbitals from the aufbau start, FP32C, the Green Iteration capped at 2
+    steps.  Checked against the oracle and the definitions:
+    - occupations: every level filled (N_e = 2 N_w), as oracle.fermi_level
+      gives for the returned eigenvalues;
+    - rho_out = 2 sum_i f_i psi_i^2 from the returned orbitals, at every
+      point of two sampled target batches, and sum rho_out w = N_e;
+    - the next input density is simple mixing on the first step;
+    - E_xc and <V_xc, rho_in> against the oracle's LDA over all points;
+    - V_H[rho_in] (the SCF's Hartree sum, the same call on the same tree)
+      against the oracle treecode on the two sampled batches, and E_H of the
+      report as 1/2 sum V_H rho_in w."""
+    wl = W.benzene_scf()
+    m = wl.mesh
+    n, nw = wl.n, wl.psi.shape[0]
+    assert 4.4e6 < n < 5.2e6 and nw == 21 and wl.n_elec == 42.0
+    with T.Tree(dev(m.xyz), dev(m.w), theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size,
+                prec=T.TAGI_FP32C) as tr:
+        vh = torch.empty(n, dtype=torch.float64, device="cuda")
+        T.tagi_fields_conv(tr.handle, None, [], None, rho=dev(wl.rho), vh=vh)
+        vh = vh.cpu().numpy()
+        with T.Scf(tr.handle, wl.n_elec, kT=KT_200K, e_zz=wl.e_zz, gi_max_iter=2, gi_store_output=True) as scf:
+            rho, psi, vx = dev(wl.rho), dev(wl.psi), dev(wl.vext)
+            ro = torch.empty(n, dtype=torch.float64, device="cuda")
+            rep = scf.step(vx, wl.vshift, rho, psi, wl.eps, rho_out=ro)
+        rho_next, psi, ro = rho.cpu().numpy(), psi.cpu().numpy(), ro.cpu().numpy()
+    w = m.w
+    assert rep["gi"]["steps"] == 2 and rep["step"] == 0
+    mu, f = oracle.fermi_level(rep["eps"], wl.n_elec, KT_200K)
+    np.testing.assert_allclose(rep["occ"], f, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(rep["occ"], 1.0, atol=1e-12)
+    ot = oracle.Tree(m.xyz, wl.leaf_size)
+    pick = np.random.default_rng(9).choice(ot.leaves, size=2, replace=False)
+    pts = np.concatenate([ot.points(c) for c in pick])
+    ref = 2.0 * np.sum(f[:, None] * psi[:, pts] ** 2, axis=0)
+    np.testing.assert_allclose(ro[pts], ref, rtol=1e-12, atol=1e-300)
+    assert abs(np.sum(ro * w) - wl.n_elec) < 1e-8 * wl.n_elec
+    np.testing.assert_allclose(rho_next, wl.rho + 0.5 * (ro - wl.rho), rtol=1e-14, atol=1e-300)
+    exc, vxc = oracle.lda_xc(wl.rho)
+    assert abs(rep["e_xc"] - np.sum(exc * wl.rho * w)) < 1e-10 * abs(rep["e_xc"])
+    assert abs(rep["e_vxc"] - np.sum(vxc * wl.rho * w)) < 1e-10 * abs(rep["e_vxc"])
+    vref = ot.treecode_batches(wl.theta, wl.degree, 1, wl.alpha, wl.rho, w, pick)
+    assert np.linalg.norm(vh[pts] - vref[pts]) < 1e-6 * np.linalg.norm(vref[pts])
+    assert abs(rep["e_hartree"] - 0.5 * np.sum(vh * wl.rho * w)) < 1e-12 * rep["e_hartree"]
+    print("C6H6 SCF step:", {k: rep[k] for k in ("e_total", "e_band", "e_hartree", "e_xc", "residual")},
+          "eps", rep["eps"])
