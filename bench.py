@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--gi-max-iter", type=int, default=60, help="c6h6 SCF: Green Iteration steps per SCF step at most")
     ap.add_argument("--tol-m", type=float, default=None, help="co/c6h6: adaptive mesh tolerance (default: the "
                                                                 "workload's, about 1.7M and 4.6M points)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick degree, theta, leaf size and the work-item segment length with the autotuner "
+                         "(quadrature-weighted error <= 1e-6) before the timed steps, and time that choice")
     return ap.parse_args()
 
 
@@ -343,20 +346,29 @@ class OracleSample:
         return inter / (t_b + share * self.t_ant), desc, outs, pts, nuc_pts
 
 
-def rel_err_vs_oracle(gpu_fields, outs, w, pts, nuc_pts):
+def rel_err_vs_oracle(gpu_fields, outs, w, pts, nuc_pts, other_scale=None):
     """Relative L2 error of the GPU's fields against the oracle treecode at
     the same (n, theta), on the sample's targets: unweighted (over mesh
     points) and quadrature-weighted, for the nucleus batches and for the
-    other sampled batches."""
+    other sampled batches.  With other_scale (batches outside the nucleus
+    set in the whole tree / those sampled) also a stratified estimate over
+    the whole mesh: the nucleus batches are all in the sample, the others a
+    seeded random sample of theirs."""
     res = {}
     other = np.setdiff1d(pts, nuc_pts)
     names = [f"psi{o}" for o in range(len(outs) - 1)] + ["hartree"]
     for name, g, ref in zip(names, gpu_fields, outs):
-        row = {}
+        row, sums = {}, {}
         for label, idx in (("nucleus", nuc_pts), ("other", other)):
             d = g[idx] - ref[idx]
-            row[label] = {"plain": float(np.linalg.norm(d) / np.linalg.norm(ref[idx])),
-                          "weighted": float(np.sqrt(np.sum(d * d * w[idx]) / np.sum(ref[idx] ** 2 * w[idx])))}
+            sums[label] = (np.sum(d * d), np.sum(ref[idx] ** 2), np.sum(d * d * w[idx]), np.sum(ref[idx] ** 2 * w[idx]))
+            row[label] = {"plain": float(np.sqrt(sums[label][0] / sums[label][1])),
+                          "weighted": float(np.sqrt(sums[label][2] / sums[label][3]))}
+        if other_scale is not None:
+            a, b = sums["nucleus"], sums["other"]
+            tot = [a[i] + other_scale * b[i] for i in range(4)]
+            row["whole_mesh_estimate"] = {"plain": float(np.sqrt(tot[0] / tot[1])),
+                                          "weighted": float(np.sqrt(tot[2] / tot[3]))}
         res[name] = row
     return res
 
@@ -376,7 +388,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(wl), "model": "oracle treecode (float64 CPU)"},
+           "config": {"workload": workload_name(wl), "segment": seg or 8192, "model": "oracle treecode (float64 CPU)"},
            "cpu_baseline": {"kind": "oracle", "value": v, "unit": UNIT, "cores": smp.threads, "sample": desc},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -577,7 +589,23 @@ def main():
     psi0 = torch.tensor(wl.psi, device=dev)
     psi = psi0.clone()
     vh = torch.empty(n, dtype=torch.float64, device=dev)
-    params = T.make_params(theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size, prec=T.TAGI_FP32C)
+    tuned = None
+    if args.autotune:
+        from paper_2003_01833_gb300 import autotune as A
+
+        t0 = time.perf_counter()
+        best, trials, ref = A.autotune(xyz, w, torch.tensor(wl.f, device=dev), list(wl.k), rho=rho, tol=1e-6,
+                                       norm="weighted", **A.grid_for(n))
+        tuned = {"norm": "weighted", "tol": 1e-6, "reference": list(ref), "trials": len(trials),
+                 "seconds": time.perf_counter() - t0,
+                 "choice": None if best is None else {"degree": best.degree, "theta": best.theta,
+                                                      "leaf_size": best.leaf_size, "segment": best.segment,
+                                                      "conv_ms": best.conv_ms, "err_weighted": best.err_weighted,
+                                                      "err_l2": best.err_l2}}
+        if best is not None:
+            wl.degree, wl.theta, wl.leaf_size = best.degree, best.theta, best.leaf_size
+    seg = tuned["choice"]["segment"] if tuned and tuned["choice"] else 0
+    params = T.make_params(theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size, prec=T.TAGI_FP32C, segment=seg)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
@@ -733,8 +761,11 @@ def main():
         gpu_fields = list(ug.cpu().numpy()) + [vh.cpu().numpy()]
         T.tagi_tree_destroy(hh)
         smp = OracleSample(wl)
-        rate, desc, outs, pts, nuc_pts = smp.run(2 * smp.threads, seed=0)
-        rel_err = rel_err_vs_oracle(gpu_fields, outs, wl.mesh.w, pts, nuc_pts)
+        nb_sample = 2 * smp.threads
+        rate, desc, outs, pts, nuc_pts = smp.run(nb_sample, seed=0)
+        n_other = len(smp.leaves) - len(smp.nuc)
+        rel_err = rel_err_vs_oracle(gpu_fields, outs, wl.mesh.w, pts, nuc_pts,
+                                    other_scale=n_other / max(1, nb_sample - len(smp.nuc)))
         smp1 = OracleSample(wl, nthreads=1)
         rate1, desc1, *_ = smp1.run(2, seed=1, with_nucleus=False)
         smp.oracle.threads(smp.threads)
@@ -744,7 +775,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32c", "data": "synthetic",
-        "config": {"workload": workload_name(wl),
+        "config": {"workload": workload_name(wl), "segment": seg or 8192,
                    "step": "tree+lists+items, fields, anterpolation, near/far kernel, SS epilogue, "
                            "eps update, MGS, residuals, E_H",
                    "interactions_per_step": inter, "near_pairs": info["near_pairs"], "far_pairs": info["far_pairs"],
@@ -761,6 +792,7 @@ def main():
                                    "(measured clock) over the per-interaction counts; not MEASURED_PEAKS.json "
                                    "(HBM and bf16 tensor peaks do not bound this kernel)"},
         "rel_err_vs_oracle": rel_err,
+        "autotune": tuned,
         "clocks": clk,
         "e2e": {"value": inter_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "s_per_step": e2e_s},

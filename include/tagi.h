@@ -45,7 +45,8 @@ typedef enum {
                        accumulation, float64 singularity-subtraction epilogue */
 } tagi_precision;
 
-/* Treecode parameters (Section 5; Eq. MAC; Algorithm 3).
+/* Treecode parameters (Section 5; Eq. MAC; Algorithm 3) and one tile shape
+ * of the near/far kernel.
  *   theta      MAC parameter, 0 <= theta < 1.  theta = 0 never approximates,
  *              so the treecode reduces to the direct sum of Eq. direct-sum.
  *   degree     interpolation degree n, 1 <= n <= 9; (n+1)^3 proxies per cluster.
@@ -54,7 +55,12 @@ typedef enum {
  *              the leaves, Section 5.1) or be 0 (taken as leaf_size).
  *   prec       TAGI_FP64 or TAGI_FP32C.
  *   ss         1: singularity subtraction (Eq. yukawa-conv-ss, coulomb-conv-ss); 0: none.
- *   alpha      Gaussian width of the Coulomb subtraction (Eq. coulomb-conv-ss), > 0. */
+ *   alpha      Gaussian width of the Coulomb subtraction (Eq. coulomb-conv-ss), > 0.
+ *   segment    sources per work item of the near/far kernel (a batch's 256
+ *              targets against a run of its interaction list), 1024 <= segment
+ *              <= 65536, or 0 for 8192.  Longer segments mean fewer partial
+ *              sums, shorter ones a finer balance of the work; the float32
+ *              sums of the FP32C form are grouped by segment. */
 typedef struct {
     double theta;
     int degree;
@@ -63,6 +69,7 @@ typedef struct {
     int prec;
     int ss;
     double alpha;
+    int segment;
 } tagi_params;
 
 typedef struct tagi_tree tagi_tree; /* opaque, owned by the library */
@@ -440,13 +447,22 @@ tagi_status tagi_scf_destroy(tagi_scf* scf);
  * norm.  Trained on converged orbitals of this solver's SCF runs; plain
  * Green Iteration measures its error.
  *
- * Model: F = 8 features, two tanh layers of H = 32 units, one output.
- * Parameters (1377 float64 values, this order): W1 (H x F row-major), b1 (H),
- * W2 (H x H row-major), b2 (H), W3 (H), b3 (1).  Weights enter the products
- * rounded to bfloat16 (nearest, ties to even); biases as float32.  The
- * arithmetic of a point is float32; gradients are summed over points in
- * float64 in a fixed order (deterministic on a given device); Adam (Kingma
- * and Ba, 2015) updates float64 master weights.
+ * Model: F = 8 features, two tanh layers of H = 32 or H = 64 units, one
+ * output.  Parameters (H F + H^2 + 3 H + 1 float64 values: 1377 for H = 32,
+ * 4801 for H = 64; this order): W1 (H x F row-major), b1 (H), W2 (H x H
+ * row-major), b2 (H), W3 (H), b3 (1).  Weights enter the products rounded to
+ * bfloat16 (nearest, ties to even); biases as float32; Adam (Kingma and Ba,
+ * 2015) updates float64 master weights.
+ *   H = 32: the arithmetic of a point is float32 (SIMT kernels); gradients
+ *     are summed over points in float64 in a fixed order.
+ *   H = 64: the three products of a point (W1 x, W2 h1, and dz2 W2 in the
+ *     gradient) and the weight-gradient sums over points run on the tensor
+ *     cores (tcgen05.mma kind::f16, bfloat16 operands, float32 accumulation),
+ *     so the second layer's input bf16(h1) and the gradient's dz2, dz1, dy
+ *     and h2 enter those products rounded to bfloat16; sums over at most 1024
+ *     points in float32, then in float64 in a fixed order.  TAGI_ERR_TIMEOUT
+ *     if a bounded wait of these kernels gave up.
+ * Both are deterministic on a given device.
  *
  * A tagi_mlp holds its weights, Adam moments and scratch: use it from one
  * stream at a time.
@@ -466,20 +482,28 @@ typedef struct {
     double eps;    /* > 0 */
 } tagi_adam_params;
 
-/* params [host] 1377 finite values; n_features must be 8 and hidden 32.
- * Synchronous (default stream).  Adam's moments start at zero. */
+/* params [host] n_params finite values (1377 for hidden = 32, 4801 for
+ * hidden = 64); n_features must be 8 and hidden 32 or 64.  Synchronous
+ * (default stream).  Adam's moments start at zero. */
 tagi_status tagi_mlp_create(int n_features, int hidden, const double* params, int64_t n_params, tagi_mlp** out);
-/* Master weights into params [host] (1377 values).  Synchronises stream. */
+/* Master weights into params [host] (the model's n_params values).
+ * Synchronises stream. */
 tagi_status tagi_mlp_get_params(const tagi_mlp* mlp, double* params, int64_t n_params, void* stream);
 /* xyz [dev] 3*n (structure of arrays); nuclei [host] n_nuclei*3 positions
  * (2..16, distinct); feat [dev] n*8 uint16 out. */
 tagi_status tagi_mlp_features(const double* xyz, int64_t n, const double* nuclei, int n_nuclei, uint16_t* feat,
                               void* stream);
+/* The same features with the two nuclei of a heteronuclear pair in list
+ * order: r1 is the distance to nuclei[0..2], r2 to nuclei[3..5] (no
+ * sorting by distance), so a point's features say which atom it is near.
+ * nuclei [host] 2*3 positions, distinct. */
+tagi_status tagi_mlp_features_ordered(const double* xyz, int64_t n, const double* nuclei, uint16_t* feat,
+                                      void* stream);
 /* y [dev] n float32 out: the network's output for each point. */
 tagi_status tagi_mlp_forward(const tagi_mlp* mlp, const uint16_t* feat, int64_t n, float* y, void* stream);
 /* Loss L = sum_p wt_p (y_p - t_p)^2 and dL/dparams of the current master
  * weights (the gradient of a rounded weight is applied to its master value):
- * target, wt [dev] n float32; grad [host] 1377 out; loss [host] out.
+ * target, wt [dev] n float32; grad [host] n_params out; loss [host] out.
  * Synchronises stream. */
 tagi_status tagi_mlp_gradient(tagi_mlp* mlp, const uint16_t* feat, const float* target, const float* wt, int64_t n,
                               double* grad, double* loss, void* stream);

@@ -55,16 +55,21 @@ def unpack(params, F: int = N_FEATURES, H: int = 32):
     return out
 
 
-def features(xyz, nuclei):
+def features(xyz, nuclei, ordered: bool = False):
     """xyz (3, n), nuclei (m, 3) with m >= 2: the bfloat16-rounded features
-    (n, 8) of the definition above."""
+    (n, 8) of the definition above.  ordered (m = 2 only): r1 and r2 are the
+    distances to the first and the second nucleus of the list, unsorted."""
     xyz = np.asarray(xyz, dtype=np.float64)
     nuc = np.asarray(nuclei, dtype=np.float64).reshape(-1, 3)
-    if nuc.shape[0] < 2:
-        raise ValueError("need two nuclei")
+    if nuc.shape[0] < 2 or (ordered and nuc.shape[0] != 2):
+        raise ValueError("need two nuclei (exactly two in list order)")
     d = np.sqrt(((xyz.T[:, None, :] - nuc[None, :, :]) ** 2).sum(axis=2))  # (n, m)
-    order = np.argsort(d, axis=1, kind="stable")
-    i1, i2 = order[:, 0], order[:, 1]
+    if ordered:
+        i1 = np.zeros(d.shape[0], dtype=np.int64)
+        i2 = np.ones(d.shape[0], dtype=np.int64)
+    else:
+        order = np.argsort(d, axis=1, kind="stable")
+        i1, i2 = order[:, 0], order[:, 1]
     rows = np.arange(d.shape[0])
     r1, r2 = d[rows, i1], d[rows, i2]
     R = np.sqrt(((nuc[i1] - nuc[i2]) ** 2).sum(axis=1))
@@ -99,6 +104,42 @@ def loss_grad(params, x, t, wt, H: int = 32, round_weights: bool = True):
     return L, np.concatenate([a.ravel() for a in g])
 
 
+# --------------------------------------------------------------------------
+# The tensor-core form (H = 64): the inputs of the three per-point products
+# and of the gradient sums over points are rounded to bfloat16, as the tensor
+# cores take them; everything else as above.
+#   forward:  h1 = tanh(x W1^T + b1), z2 = bf16(h1) W2^T + b2, h2 = tanh z2,
+#             y = W3 . h2 + b3;
+#   gradient: dy = 2 wt (y - t), dz2 = dy W3 (1 - h2^2),
+#             dz1 = (bf16(dz2) W2) (1 - h1^2),
+#             dW1 = bf16(dz1)^T x, db1 = sum bf16(dz1),
+#             dW2 = bf16(dz2)^T bf16(h1), db2 = sum bf16(dz2),
+#             dW3 = bf16(dy) bf16(h2), db3 = sum bf16(dy).
+# (W1, W2, W3 rounded to bfloat16 and x bfloat16 as before.)
+# --------------------------------------------------------------------------
+def forward_tc(params, x, H: int = 64):
+    W1, b1, W2, b2, W3, b3 = unpack(params, x.shape[1], H)
+    W1, W2, W3 = bf16_round(W1), bf16_round(W2), bf16_round(W3)
+    h1 = np.tanh(x @ W1.T + b1)
+    h1b = bf16_round(h1)
+    h2 = np.tanh(h1b @ W2.T + b2)
+    return h2 @ W3 + b3[0], (h1, h1b, h2)
+
+
+def loss_grad_tc(params, x, t, wt, H: int = 64):
+    W1, b1, W2, b2, W3, b3 = unpack(params, x.shape[1], H)
+    W2r, W3r = bf16_round(W2), bf16_round(W3)
+    y, (h1, h1b, h2) = forward_tc(params, x, H)
+    r = y - t
+    L = float(np.sum(wt * r * r))
+    dy = 2.0 * wt * r
+    dz2b = bf16_round(dy[:, None] * W3r[None, :] * (1.0 - h2 * h2))
+    dz1b = bf16_round((dz2b @ W2r) * (1.0 - h1 * h1))
+    dyb, h2b = bf16_round(dy), bf16_round(h2)
+    g = [dz1b.T @ x, dz1b.sum(0), dz2b.T @ h1b, dz2b.sum(0), dyb @ h2b, np.array([dyb.sum()])]
+    return L, np.concatenate([a.ravel() for a in g])
+
+
 def adam_step(params, m, v, g, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update at step t >= 1; returns (params, m, v)."""
     m = beta1 * m + (1.0 - beta1) * g
@@ -108,22 +149,22 @@ def adam_step(params, m, v, g, t: int, lr: float, beta1=0.9, beta2=0.999, eps=1e
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def train(params, x, t, wt, steps: int, lr, H: int = 32, beta1=0.9, beta2=0.999, eps=1e-8):
-    """Full-batch Adam; lr is a number or a function of the step (1-based).
-    Returns (params, losses before each update)."""
+def train(params, x, t, wt, steps: int, lr, H: int = 32, beta1=0.9, beta2=0.999, eps=1e-8, tc: bool = False):
+    """Full-batch Adam; lr is a number or a function of the step (1-based);
+    tc: the tensor-core form.  Returns (params, losses before each update)."""
     p = np.asarray(params, dtype=np.float64).copy()
     m = np.zeros_like(p)
     v = np.zeros_like(p)
     losses = []
     for k in range(1, steps + 1):
-        L, g = loss_grad(p, x, t, wt, H)
+        L, g = loss_grad_tc(p, x, t, wt, H) if tc else loss_grad(p, x, t, wt, H)
         losses.append(L)
         p, m, v = adam_step(p, m, v, g, k, lr(k) if callable(lr) else lr, beta1, beta2, eps)
     return p, np.array(losses)
 
 
-def warm_start(params, x, s, w, H: int = 32):
+def warm_start(params, x, s, w, H: int = 32, tc: bool = False):
     """psi = s (1 + y) normalised in the quadrature-weighted norm."""
-    y, _ = forward(params, x, H)
+    y, _ = forward_tc(params, x, H) if tc else forward(params, x, H)
     psi = s * (1.0 + y)
     return psi / np.sqrt(np.sum(psi * psi * w))

@@ -1,11 +1,14 @@
 """Choice of the treecode parameters -- interpolation degree n, MAC theta and
-leaf size N_L (Section 5) -- under an error bar, for one mesh and one set of
-fields.
+leaf size N_L (Section 5) -- and of the near/far kernel's work-item segment
+length (sources per item: a tile shape of the kernel) under an error bar, for
+one mesh and one set of fields.
 
 Every candidate builds its tree and runs the one-pass convolution of the
 fields (tagi_fields_conv, the work of a Green iteration on a tree built once).
 Its error is the relative L2 norm per field against a tight reference
-configuration evaluated in the plain float64 form, in one of two norms: the
+configuration evaluated in the plain float64 form (or, on meshes where that
+form is too slow, the FP32C form at the tight configuration, whose own error
+is ~1e-7), in one of two norms: the
 plain one over mesh points, or the quadrature-weighted one that Green
 Iteration's convergence test uses.  The choice is the candidate with the
 shortest convolution time whose largest error in the chosen norm stays below
@@ -34,6 +37,7 @@ class Trial:
     degree: int
     theta: float
     leaf_size: int
+    segment: int
     build_ms: float
     conv_ms: float
     max_rel_err: float
@@ -56,12 +60,12 @@ def _conv(tree, f, k, rho, u, vh):
     T.tagi_fields_conv(tree.handle, f, k, u, rho=rho, vh=vh)
 
 
-def _measure(xyz, w, f, k, rho, degree, theta, leaf_size, prec, reps):
+def _measure(xyz, w, f, k, rho, degree, theta, leaf_size, prec, reps, segment=0):
     import torch
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tree = T.Tree(xyz, w, theta=theta, degree=degree, leaf_size=leaf_size, prec=prec)
+    tree = T.Tree(xyz, w, theta=theta, degree=degree, leaf_size=leaf_size, prec=prec, segment=segment)
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
     try:
@@ -98,7 +102,8 @@ def rel_errors(rows, ref_rows, w):
 
 
 def autotune(xyz, w, f, k, rho=None, tol=1e-6, norm="l2", degrees=(6, 8), thetas=(0.5, 0.6, 0.7, 0.8),
-             leaf_sizes=(1000, 2000, 4000), reference=(8, 0.4, 2000), prec=None, prec_ref=None, reps=3):
+             leaf_sizes=(1000, 2000, 4000), segments=(8192,), reference=(8, 0.4, 2000), prec=None, prec_ref=None,
+             reps=3):
     """xyz (3, n), w (n,), f (nf, n), rho (n,) or None: float64 CUDA tensors;
     k: nf decay rates; norm: "l2" or "weighted".  The candidates run in prec
     (FP32C by default), the reference in prec_ref (the plain float64 form by
@@ -114,10 +119,22 @@ def autotune(xyz, w, f, k, rho=None, tol=1e-6, norm="l2", degrees=(6, 8), thetas
     for n in degrees:
         for th in thetas:
             for nl in leaf_sizes:
-                b_ms, c_ms, rows, inter = _measure(xyz, w, f, k, rho, n, th, nl, prec, reps)
-                l2, wt = rel_errors(rows, ref_rows, wh)
-                trials.append(Trial(n, th, nl, b_ms, c_ms, l2 if norm == "l2" else wt, int(inter), l2, wt))
+                for sg in segments:
+                    b_ms, c_ms, rows, inter = _measure(xyz, w, f, k, rho, n, th, nl, prec, reps, sg)
+                    l2, wt = rel_errors(rows, ref_rows, wh)
+                    trials.append(Trial(n, th, nl, sg, b_ms, c_ms, l2 if norm == "l2" else wt, int(inter), l2, wt))
     return select(trials, tol), trials, reference
+
+
+def grid_for(n):
+    """The search grid for an n-point mesh: the full grid (with segment
+    lengths 4096, 8192 and 16384) up to 400,000 points; above that a
+    narrower one and the FP32C form as the reference (the plain float64 form
+    takes minutes per convolution there)."""
+    if n <= 400_000:
+        return {"segments": (4096, 8192, 16384)}
+    return {"degrees": (6, 8), "thetas": (0.6, 0.7, 0.8), "leaf_sizes": (2000, 4000), "segments": (8192, 16384),
+            "prec_ref": T.TAGI_FP32C, "reps": 2}
 
 
 def report(best, trials, reference, tol, norm="l2"):
@@ -138,15 +155,15 @@ def main(argv=None):
     from . import workloads as W
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="li-small", choices=["li", "li-small", "h"])
+    ap.add_argument("--workload", default="li-small", choices=["li", "li-small", "h", "co"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--norm", default="l2", choices=["l2", "weighted"])
     a = ap.parse_args(argv)
     wl = {"li": lambda: W.lithium(), "li-small": lambda: W.lithium(tol_m=1e-3),
-          "h": lambda: W.hydrogen_adaptive()}[a.workload]()
+          "h": lambda: W.hydrogen_adaptive(), "co": lambda: W.carbon_monoxide()}[a.workload]()
     dev = lambda x: torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
     best, trials, ref = autotune(dev(wl.mesh.xyz), dev(wl.mesh.w), dev(wl.f), list(wl.k), rho=dev(wl.rho),
-                                 tol=a.tol, norm=a.norm)
+                                 tol=a.tol, norm=a.norm, **grid_for(wl.n))
     out = report(best, trials, ref, a.tol, a.norm)
     out["workload"] = {"name": wl.name, "points": int(wl.n), "fields": int(len(wl.k)) + 1}
     print(json.dumps(out))

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtagi.so")
-SOURCES = ["api.cu", "alloc.cu", "tree.cu", "anterp.cu", "interact.cu", "green.cu", "iterate.cu", "noalloc.cu", "mlp.cu", "unitrates.cu", "batches.cu"]
+SOURCES = ["api.cu", "alloc.cu", "tree.cu", "anterp.cu", "interact.cu", "green.cu", "iterate.cu", "noalloc.cu", "mlp.cu", "unitrates.cu", "batches.cu", "mlp64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

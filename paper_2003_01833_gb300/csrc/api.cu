@@ -286,7 +286,9 @@ tagi_status tagi_tree_build(const double* xyz, const double* w, int64_t n, const
         TAGI_REQUIRE(p.prec == TAGI_FP64 || p.prec == TAGI_FP32C, "prec must be TAGI_FP64 or TAGI_FP32C");
         TAGI_REQUIRE(p.ss == 0 || p.ss == 1, "ss must be 0 or 1");
         TAGI_REQUIRE(std::isfinite(p.alpha) && p.alpha > 0.0, "alpha must be finite and > 0");
+        TAGI_REQUIRE(p.segment == 0 || (p.segment >= 1024 && p.segment <= 65536), "segment must be 0 or in [1024, 65536]");
         std::unique_ptr<Tree> T(new Tree());
+        T->segment = p.segment ? p.segment : 8192;
         T->n = n;
         T->theta = p.theta;
         T->degree = p.degree;

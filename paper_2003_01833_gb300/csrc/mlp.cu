@@ -1,6 +1,7 @@
 // Learned warm start for SCF runs of molecules: point features, a per-point
-// MLP (F = 8 inputs, two tanh layers of H = 32, one output), its gradient and
-// Adam.  Weights enter the products rounded to bfloat16 and features are
+// MLP (F = 8 inputs, two tanh layers of H = 32 here, one output), its
+// gradient and Adam.  The H = 64 network runs on the tensor cores
+// (mlp64.cu); this file holds the entry points of both.  Weights enter the products rounded to bfloat16 and features are
 // stored as bfloat16; the arithmetic of a point is float32, gradients are
 // accumulated over points in float64 in a fixed order (deterministic for a
 // given device), and Adam keeps float64 master weights.
@@ -42,6 +43,7 @@ constexpr size_t kGradSmem = sizeof(float) * (kPPad + (size_t)kThreads * kStride
 struct Nuclei {
     double x[kMaxNuclei], y[kMaxNuclei], z[kMaxNuclei];
     int m;
+    int ordered;  // 1: two nuclei taken in list order (r1 to the first) instead of by distance
 };
 
 // Nearest bfloat16 value of x, ties to even, from the float64 value: x / q
@@ -117,7 +119,7 @@ __global__ void k_features(const double* __restrict__ xyz, int64_t n, Nuclei nuc
     const double px = xyz[i], py = xyz[n + i], pz = xyz[2 * n + i];
     double d1 = INFINITY, d2 = INFINITY;
     int a1 = 0, a2 = 1;
-    for (int a = 0; a < nuc.m; a++) {
+    for (int a = 0; a < (nuc.ordered ? 0 : nuc.m); a++) {
         const double dx = px - nuc.x[a], dy = py - nuc.y[a], dz = pz - nuc.z[a];
         const double d = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
         if (d < d1) {
@@ -129,6 +131,12 @@ __global__ void k_features(const double* __restrict__ xyz, int64_t n, Nuclei nuc
             d2 = d;
             a2 = a;
         }
+    }
+    if (nuc.ordered) {
+        const double dx1 = px - nuc.x[0], dy1 = py - nuc.y[0], dz1 = pz - nuc.z[0];
+        const double dx2 = px - nuc.x[1], dy2 = py - nuc.y[1], dz2 = pz - nuc.z[1];
+        d1 = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx1, dx1), __dmul_rn(dy1, dy1)), __dmul_rn(dz1, dz1)));
+        d2 = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx2, dx2), __dmul_rn(dy2, dy2)), __dmul_rn(dz2, dz2)));
     }
     const double ex = nuc.x[a1] - nuc.x[a2], ey = nuc.y[a1] - nuc.y[a2], ez = nuc.z[a1] - nuc.z[a2];
     const double R = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
@@ -302,19 +310,19 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const uint16_t* __restric
     }
 }
 
-// Gradient and loss from the per-block partials (block order), then, if
-// apply, one Adam step on the float64 master weights (c1 = 1 - beta1^t,
-// c2 = 1 - beta2^t).
-__global__ void k_mlp_adam(const double* __restrict__ partial, int nblk, double* __restrict__ master,
+// Gradient and loss from the per-block partials [nblk][np + 1] (block
+// order), then, if apply, one Adam step on the float64 master weights
+// (c1 = 1 - beta1^t, c2 = 1 - beta2^t).
+__global__ void k_mlp_adam(const double* __restrict__ partial, int nblk, int np, double* __restrict__ master,
                            double* __restrict__ m, double* __restrict__ v, double lr, double beta1, double beta2,
                            double eps, double c1, double c2, int apply, double* __restrict__ grad_out,
                            double* __restrict__ loss_out)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e > kP) return;
+    if (e > np) return;
     double g = 0.0;
-    for (int b = 0; b < nblk; b++) g += partial[(size_t)b * (kP + 1) + e];
-    if (e == kP) {
+    for (int b = 0; b < nblk; b++) g += partial[(size_t)b * (np + 1) + e];
+    if (e == np) {
         *loss_out = g;
         return;
     }
@@ -367,8 +375,10 @@ __global__ void k_warm_scale(double* __restrict__ psi, int64_t n, const double* 
 struct Mlp {
     int dev = 0;
     int sms = 0;
+    int H = kH;     // 32: SIMT kernels of this file; 64: tensor-core kernels (mlp64.cu)
+    int np = kP;    // parameters
     int64_t step = 0;
-    DevBuf master, m, v, partial, grad, loss, part;
+    DevBuf master, m, v, partial, grad, loss, part, errd;
     std::string err;
 };
 
@@ -416,10 +426,13 @@ void check_data(const void* feat, int64_t n)
 void grad_pass(Mlp& M, const uint16_t* feat, const float* target, const float* wt, int64_t n,
                const tagi_adam_params* a, bool apply, cudaStream_t s)
 {
-    const int grid = grad_grid(M, n);
-    M.partial.ensure(sizeof(double) * (size_t)grid * (kP + 1));
-    launch(k_mlp_grad, grid, kThreads, kGradSmem, s, feat, target, wt, n, M.master.as<double>(),
-           M.partial.as<double>());
+    const int grid = M.H == 64 ? mlp64_grad_grid(n, M.sms) : grad_grid(M, n);
+    M.partial.ensure(sizeof(double) * (size_t)grid * (M.np + 1));
+    if (M.H == 64)
+        mlp64_gradient(feat, target, wt, n, M.master.as<double>(), M.partial.as<double>(), grid, M.errd.as<int>(), s);
+    else
+        launch(k_mlp_grad, grid, kThreads, kGradSmem, s, feat, target, wt, n, M.master.as<double>(),
+               M.partial.as<double>());
     double c1 = 1.0, c2 = 1.0, lr = 0.0, b1 = 0.9, b2 = 0.999, eps = 1e-8;
     if (apply) {
         M.step += 1;
@@ -430,10 +443,32 @@ void grad_pass(Mlp& M, const uint16_t* feat, const float* target, const float* w
         c1 = 1.0 - std::pow(b1, (double)M.step);
         c2 = 1.0 - std::pow(b2, (double)M.step);
     }
-    launch(k_mlp_adam, (kP + 1 + 127) / 128, 128, 0, s, M.partial.as<double>(), grid, M.master.as<double>(),
+    launch(k_mlp_adam, (M.np + 1 + 127) / 128, 128, 0, s, M.partial.as<double>(), grid, M.np, M.master.as<double>(),
            M.m.as<double>(), M.v.as<double>(), lr, b1, b2, eps, c1, c2, apply ? 1 : 0, M.grad.as<double>(),
            M.loss.as<double>());
     TAGI_LAUNCH_CHECK();
+}
+
+// y of the network for n points (the H = 32 or the H = 64 kernels)
+void run_forward(Mlp& M, const uint16_t* feat, int64_t n, float* y, cudaStream_t s)
+{
+    if (M.H == 64) {
+        mlp64_forward(feat, n, M.master.as<double>(), y, M.errd.as<int>(), M.sms, s);
+    } else {
+        const int64_t blocks = std::min<int64_t>((n + kThreads - 1) / kThreads, 8LL * M.sms);
+        launch(k_mlp_forward, (unsigned)blocks, kThreads, 0, s, feat, n, M.master.as<double>(), y);
+        TAGI_LAUNCH_CHECK();
+    }
+}
+
+// after a synchronisation: a bounded wait of the tensor-core kernels gave up
+void check_mlp_err(Mlp& M, cudaStream_t s)
+{
+    if (M.H != 64) return;
+    int h = 0;
+    TAGI_CUDA(cudaMemcpyAsync(&h, M.errd.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TAGI_CUDA(cudaStreamSynchronize(s));
+    if (h) throw Error(TAGI_ERR_TIMEOUT, "a bounded wait of the tensor-core MLP kernels gave up");
 }
 
 }  // namespace
@@ -448,23 +483,29 @@ tagi_status tagi_mlp_create(int n_features, int hidden, const double* params, in
     return guarded_mlp([&] {
         TAGI_REQUIRE(out != nullptr, "out is NULL");
         *out = nullptr;
-        TAGI_REQUIRE(n_features == kF && hidden == kH, "the model has 8 features and 32 hidden units");
-        TAGI_REQUIRE(params != nullptr && n_params == kP, "params must hold 1377 values");
+        TAGI_REQUIRE(n_features == kF && (hidden == kH || hidden == 64),
+                     "the model has 8 features and 32 or 64 hidden units");
+        const int np = hidden == 64 ? mlp64_params() : kP;
+        TAGI_REQUIRE(params != nullptr && n_params == np, "params must hold 1377 (H = 32) or 4801 (H = 64) values");
         for (int64_t e = 0; e < n_params; e++) TAGI_REQUIRE(std::isfinite(params[e]), "params must be finite");
         TAGI_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem));
         auto* M = new Mlp();
+        M->H = hidden;
+        M->np = np;
         try {
             TAGI_CUDA(cudaGetDevice(&M->dev));
             TAGI_CUDA(cudaDeviceGetAttribute(&M->sms, cudaDevAttrMultiProcessorCount, M->dev));
             AllocStream as(nullptr);
-            M->master.ensure(sizeof(double) * kP);
-            M->m.ensure(sizeof(double) * kP);
-            M->v.ensure(sizeof(double) * kP);
-            M->grad.ensure(sizeof(double) * kP);
+            M->master.ensure(sizeof(double) * np);
+            M->m.ensure(sizeof(double) * np);
+            M->v.ensure(sizeof(double) * np);
+            M->grad.ensure(sizeof(double) * np);
             M->loss.ensure(sizeof(double));
-            TAGI_CUDA(cudaMemcpy(M->master.p, params, sizeof(double) * kP, cudaMemcpyHostToDevice));
-            TAGI_CUDA(cudaMemset(M->m.p, 0, sizeof(double) * kP));
-            TAGI_CUDA(cudaMemset(M->v.p, 0, sizeof(double) * kP));
+            M->errd.ensure(sizeof(int));
+            TAGI_CUDA(cudaMemcpy(M->master.p, params, sizeof(double) * np, cudaMemcpyHostToDevice));
+            TAGI_CUDA(cudaMemset(M->m.p, 0, sizeof(double) * np));
+            TAGI_CUDA(cudaMemset(M->v.p, 0, sizeof(double) * np));
+            TAGI_CUDA(cudaMemset(M->errd.p, 0, sizeof(int)));
         } catch (...) {
             delete M;
             throw;
@@ -477,22 +518,25 @@ tagi_status tagi_mlp_get_params(const tagi_mlp* mlp, double* params, int64_t n_p
 {
     return guarded_mlp([&] {
         Mlp* M = as_mlp(mlp);
-        TAGI_REQUIRE(params != nullptr && n_params == kP, "params must hold 1377 values");
+        TAGI_REQUIRE(params != nullptr && n_params == M->np, "params must hold the model's parameter count");
         cudaStream_t s = (cudaStream_t)stream;
-        TAGI_CUDA(cudaMemcpyAsync(params, M->master.p, sizeof(double) * kP, cudaMemcpyDeviceToHost, s));
+        TAGI_CUDA(cudaMemcpyAsync(params, M->master.p, sizeof(double) * M->np, cudaMemcpyDeviceToHost, s));
         TAGI_CUDA(cudaStreamSynchronize(s));
+        check_mlp_err(*M, s);
     });
 }
 
-tagi_status tagi_mlp_features(const double* xyz, int64_t n, const double* nuclei, int n_nuclei, uint16_t* feat,
-                              void* stream)
+static tagi_status features_call(const double* xyz, int64_t n, const double* nuclei, int n_nuclei, int ordered,
+                          uint16_t* feat, void* stream)
 {
     return guarded_mlp([&] {
         TAGI_REQUIRE(xyz != nullptr && nuclei != nullptr, "xyz or nuclei is NULL");
         check_data(feat, n);
         TAGI_REQUIRE(n_nuclei >= 2 && n_nuclei <= kMaxNuclei, "need 2 to 16 nuclei");
+        TAGI_REQUIRE(!ordered || n_nuclei == 2, "list order needs exactly two nuclei");
         Nuclei nu{};
         nu.m = n_nuclei;
+        nu.ordered = ordered;
         for (int a = 0; a < n_nuclei; a++) {
             nu.x[a] = nuclei[3 * a];
             nu.y[a] = nuclei[3 * a + 1];
@@ -509,16 +553,25 @@ tagi_status tagi_mlp_features(const double* xyz, int64_t n, const double* nuclei
     });
 }
 
+tagi_status tagi_mlp_features(const double* xyz, int64_t n, const double* nuclei, int n_nuclei, uint16_t* feat,
+                              void* stream)
+{
+    return features_call(xyz, n, nuclei, n_nuclei, 0, feat, stream);
+}
+
+tagi_status tagi_mlp_features_ordered(const double* xyz, int64_t n, const double* nuclei, uint16_t* feat,
+                                      void* stream)
+{
+    return features_call(xyz, n, nuclei, 2, 1, feat, stream);
+}
+
 tagi_status tagi_mlp_forward(const tagi_mlp* mlp, const uint16_t* feat, int64_t n, float* y, void* stream)
 {
     return guarded_mlp([&] {
         Mlp* M = as_mlp(mlp);
         check_data(feat, n);
         TAGI_REQUIRE(y != nullptr, "y is NULL");
-        const int64_t blocks = std::min<int64_t>((n + kThreads - 1) / kThreads, 8LL * M->sms);
-        launch(k_mlp_forward, (unsigned)blocks, kThreads, 0, (cudaStream_t)stream, feat, n, M->master.as<double>(),
-               y);
-        TAGI_LAUNCH_CHECK();
+        run_forward(*M, feat, n, y, (cudaStream_t)stream);
     });
 }
 
@@ -533,9 +586,10 @@ tagi_status tagi_mlp_gradient(tagi_mlp* mlp, const uint16_t* feat, const float* 
         cudaStream_t s = (cudaStream_t)stream;
         AllocStream as(s);
         grad_pass(*M, feat, target, wt, n, nullptr, false, s);
-        TAGI_CUDA(cudaMemcpyAsync(grad, M->grad.p, sizeof(double) * kP, cudaMemcpyDeviceToHost, s));
+        TAGI_CUDA(cudaMemcpyAsync(grad, M->grad.p, sizeof(double) * M->np, cudaMemcpyDeviceToHost, s));
         TAGI_CUDA(cudaMemcpyAsync(loss, M->loss.p, sizeof(double), cudaMemcpyDeviceToHost, s));
         TAGI_CUDA(cudaStreamSynchronize(s));
+        check_mlp_err(*M, s);
     });
 }
 
@@ -556,6 +610,7 @@ tagi_status tagi_mlp_train_step(tagi_mlp* mlp, const uint16_t* feat, const float
         if (loss) {
             TAGI_CUDA(cudaMemcpyAsync(loss, M->loss.p, sizeof(double), cudaMemcpyDeviceToHost, s));
             TAGI_CUDA(cudaStreamSynchronize(s));
+            check_mlp_err(*M, s);
         }
     });
 }
@@ -571,8 +626,7 @@ tagi_status tagi_mlp_warm_start(const tagi_mlp* mlp, const uint16_t* feat, const
         AllocStream as(s);
         DevBuf y;
         y.ensure(sizeof(float) * (size_t)n);
-        const int64_t fb = std::min<int64_t>((n + kThreads - 1) / kThreads, 8LL * M->sms);
-        launch(k_mlp_forward, (unsigned)fb, kThreads, 0, s, feat, n, M->master.as<double>(), y.as<float>());
+        run_forward(*M, feat, n, y.as<float>(), s);
         const int nb = (int)std::min<int64_t>((n + 255) / 256, 4LL * M->sms);
         M->part.ensure(sizeof(double) * nb);
         launch(k_warm_apply, nb, 256, 0, s, (const float*)y.as<float>(), s0, w, n, psi, M->part.as<double>());

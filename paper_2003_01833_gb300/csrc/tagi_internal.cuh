@@ -143,6 +143,7 @@ struct Tree {
     int prec = TAGI_FP32C;
     int ss = 1;
     double alpha = 1.0;
+    int segment = 8192;  // sources per work item of the near/far kernel
     int P = 0;  // (degree+1)^3
     cudaStream_t stream = nullptr;
 
@@ -268,6 +269,13 @@ struct Scf {
 };
 void scf_step(Scf& S, const double* vext, double vshift, double* rho, double* psi, double* eps, int nw,
               double* occ, double* rho_out, tagi_scf_report* rep);
+
+// mlp64.cu: the H = 64 warm-start network on the tensor cores
+int mlp64_params();
+void mlp64_forward(const uint16_t* feat, int64_t n, const double* master, float* y, int* err, int sms, cudaStream_t s);
+int mlp64_grad_grid(int64_t n, int sms);
+void mlp64_gradient(const uint16_t* feat, const float* target, const float* wt, int64_t n, const double* master,
+                    double* partial, int grid, int* err, cudaStream_t s);
 
 // sets the message tagi_last_error returns on this thread; returns status
 tagi_status report_error(tagi_status status, const char* msg);

@@ -979,7 +979,7 @@ void build_tree(Tree& T, const double* xyz, const double* w)
     TAGI_LAUNCH_CHECK();
 
     // ---- work items of the near/far kernel
-    const int seg_src = 8192;
+    const int seg_src = T.segment;
     DevBuf nch, nit, choff, itoff;
     nch.ensure(8 * (size_t)nleaf);
     nit.ensure(8 * (size_t)nleaf);

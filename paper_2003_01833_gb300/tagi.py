@@ -39,7 +39,7 @@ class TagiError(RuntimeError):
 class tagi_params(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("degree", ctypes.c_int), ("leaf_size", ctypes.c_int),
                 ("batch_size", ctypes.c_int), ("prec", ctypes.c_int), ("ss", ctypes.c_int),
-                ("alpha", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("segment", ctypes.c_int)]
 
 
 class tagi_tree_stats(ctypes.Structure):
@@ -140,6 +140,8 @@ def lib():
         L.tagi_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, _D, ctypes.c_int64, ctypes.POINTER(_vp)]
         L.tagi_mlp_get_params.argtypes = [_vp, _D, ctypes.c_int64, _vp]
         L.tagi_mlp_features.argtypes = [_vp, ctypes.c_int64, _D, ctypes.c_int, _vp, _vp]
+        L.tagi_mlp_features_ordered.argtypes = [_vp, ctypes.c_int64, _D, _vp, _vp]
+        L.tagi_mlp_features_ordered.restype = ctypes.c_int
         L.tagi_mlp_forward.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
         L.tagi_mlp_gradient.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _D, _D, _vp]
         L.tagi_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(tagi_adam_params),
@@ -191,9 +193,9 @@ def _hd(a):
     return a, a.ctypes.data_as(_D)
 
 
-def make_params(theta=0.7, degree=8, leaf_size=2000, prec=TAGI_FP32C, ss=True, alpha=1.0):
+def make_params(theta=0.7, degree=8, leaf_size=2000, prec=TAGI_FP32C, ss=True, alpha=1.0, segment=0):
     return tagi_params(float(theta), int(degree), int(leaf_size), int(leaf_size), int(prec), int(bool(ss)),
-                       float(alpha))
+                       float(alpha), int(segment))
 
 
 # ----------------------------------------------------------------- C ABI names
@@ -593,6 +595,12 @@ MLP_HIDDEN = 32
 MLP_PARAMS = 1377
 
 
+def mlp_params(hidden: int) -> int:
+    """Parameter count of the warm-start network with `hidden` units."""
+    F, H = MLP_FEATURES, hidden
+    return H * F + H + H * H + H + H + 1
+
+
 def _tptr(t, name, dtype, numel):
     """Device pointer of a contiguous CUDA tensor of the given dtype."""
     import torch
@@ -604,17 +612,25 @@ def _tptr(t, name, dtype, numel):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def tagi_mlp_features(xyz, nuclei, feat=None, stream=None):
+def tagi_mlp_features(xyz, nuclei, feat=None, stream=None, ordered=False):
     """xyz (3, n) float64 CUDA; nuclei (m, 3) host positions.  Returns the
-    (n, 8) bfloat16 encodings as an int16 CUDA tensor (feat if given)."""
+    (n, 8) bfloat16 encodings as an int16 CUDA tensor (feat if given).
+    ordered: two nuclei in list order (tagi_mlp_features_ordered)."""
     import torch
 
     n = xyz.numel() // 3
     nu = np.ascontiguousarray(np.asarray(nuclei, dtype=np.float64).reshape(-1, 3))
     if feat is None:
         feat = torch.empty((n, MLP_FEATURES), dtype=torch.int16, device=xyz.device)
-    _check(lib().tagi_mlp_features(_dptr(xyz, "xyz", 3 * n), n, nu.ctypes.data_as(_D), nu.shape[0],
-                                   _tptr(feat, "feat", torch.int16, n * MLP_FEATURES), _stream(stream)))
+    fp = _tptr(feat, "feat", torch.int16, n * MLP_FEATURES)
+    if ordered:
+        if nu.shape[0] != 2:
+            raise ValueError("list order needs exactly two nuclei")
+        _check(lib().tagi_mlp_features_ordered(_dptr(xyz, "xyz", 3 * n), n, nu.ctypes.data_as(_D), fp,
+                                               _stream(stream)))
+    else:
+        _check(lib().tagi_mlp_features(_dptr(xyz, "xyz", 3 * n), n, nu.ctypes.data_as(_D), nu.shape[0], fp,
+                                       _stream(stream)))
     return feat
 
 
@@ -622,15 +638,17 @@ class Mlp:
     """Warm-start MLP on the device (tagi_mlp_*).  Use as a context manager
     or call close()."""
 
-    def __init__(self, params):
+    def __init__(self, params, hidden=MLP_HIDDEN):
         p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
         h = _vp()
-        _check(lib().tagi_mlp_create(MLP_FEATURES, MLP_HIDDEN, p.ctypes.data_as(_D), p.size, ctypes.byref(h)))
+        _check(lib().tagi_mlp_create(MLP_FEATURES, int(hidden), p.ctypes.data_as(_D), p.size, ctypes.byref(h)))
         self.handle = h
+        self.hidden = int(hidden)
+        self.n_params = mlp_params(self.hidden)
 
     def params(self, stream=None):
-        out = np.empty(MLP_PARAMS)
-        _check(lib().tagi_mlp_get_params(self.handle, out.ctypes.data_as(_D), MLP_PARAMS, _stream(stream)))
+        out = np.empty(self.n_params)
+        _check(lib().tagi_mlp_get_params(self.handle, out.ctypes.data_as(_D), self.n_params, _stream(stream)))
         return out
 
     def _data(self, feat, target=None, wt=None):
@@ -654,7 +672,7 @@ class Mlp:
     def gradient(self, feat, target, wt, stream=None):
         """(loss, gradient) of the current master weights."""
         n, (fp, tp, wp) = self._data(feat, target, wt)
-        g = np.empty(MLP_PARAMS)
+        g = np.empty(self.n_params)
         loss = np.zeros(1)
         _check(lib().tagi_mlp_gradient(self.handle, fp, tp, wp, n, g.ctypes.data_as(_D), loss.ctypes.data_as(_D),
                                        _stream(stream)))

@@ -15,7 +15,13 @@ sum_p w_p s_p^2 (y_p - t_p)^2, which is the squared orbital error
 ||psi_warm - psi*||_w^2 before normalisation.
 
 The data set of H2 runs: `h2_bond_lengths` (32 seeded bond lengths in
-[1, 2] Bohr), meshes from `workloads.hydrogen_molecule`.
+[1, 2] Bohr), meshes from `workloads.hydrogen_molecule`.  The network has 64
+hidden units by default (the tensor-core kernels; 32 selects the SIMT ones).
+
+Measure: an SCF run ends when ||rho_out - rho_in||_w < tol_scf and the
+total energy has settled, |E_k - E_{k-1}| < 1e-6 Ha; the steps, Green
+iterations and wall time until the energy first settles are reported for
+both starts.
 """
 from __future__ import annotations
 
@@ -32,7 +38,11 @@ def _dev(torch, a, device="cuda"):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
 
 
-def scf_run(wl, psi0=None, eps0=None, rho0=None, tol_scf=1e-4, max_steps=40, prec=None, store_output=True):
+E_TOL = 1e-6  # Ha: the total energy has settled when successive SCF steps differ by less
+
+
+def scf_run(wl, psi0=None, eps0=None, rho0=None, tol_scf=1e-4, max_steps=40, prec=None, store_output=True,
+            e_tol=E_TOL):
     """SCF iteration on the device from (psi0, eps0, rho0) (the workload's
     superposition start where None) until ||rho_out - rho_in||_w < tol_scf.
     Returns the converged orbitals (host), eigenvalues, energy and the cost:
@@ -60,18 +70,24 @@ def scf_run(wl, psi0=None, eps0=None, rho0=None, tol_scf=1e-4, max_steps=40, pre
                                         gi_store_output=store_output) as scf:
         rho, psi, vx = _dev(torch, rho0), _dev(torch, psi0), _dev(torch, wl.vext)
         rep = None
+        settled = None  # (steps, Green iterations, seconds) when |dE| < e_tol first held
         for _ in range(max_steps):
             rep = scf.step(vx, wl.vshift, rho, psi, eps)
             eps = rep["eps"]
             hist.append({"residual": rep["residual"], "e_total": rep["e_total"], "gi_steps": rep["gi"]["steps"],
-                         "eps": [float(e) for e in eps]})
-            if rep["residual"] < tol_scf:
+                         "eps": [float(e) for e in eps], "seconds": time.perf_counter() - t0})
+            if settled is None and len(hist) > 1 and abs(hist[-1]["e_total"] - hist[-2]["e_total"]) < e_tol:
+                settled = (len(hist), int(sum(h["gi_steps"] for h in hist)), hist[-1]["seconds"])
+            if rep["residual"] < tol_scf and settled is not None:
                 break
         psi_h = psi.cpu().numpy()
+        rho_h = rho.cpu().numpy()
     torch.cuda.synchronize()
-    return {"psi": psi_h, "eps": np.array(eps), "e_total": rep["e_total"], "converged": rep["residual"] < tol_scf,
+    return {"psi": psi_h, "rho": rho_h, "eps": np.array(eps), "e_total": rep["e_total"], "converged": rep["residual"] < tol_scf,
             "scf_steps": len(hist), "gi_steps": int(sum(h["gi_steps"] for h in hist)), "history": hist,
-            "seconds": time.perf_counter() - t0}
+            "seconds": time.perf_counter() - t0,
+            "energy_settled": None if settled is None else {"scf_steps": settled[0], "gi_steps": settled[1],
+                                                            "seconds": settled[2], "e_tol": e_tol}}
 
 
 def generate(bond_lengths, tol_m=3e-6, tol_scf=1e-4, log=print):
@@ -121,7 +137,7 @@ def cosine_lr(lr0, steps):
     return lambda k: 0.5 * lr0 * (1.0 + np.cos(np.pi * (k - 1) / steps))
 
 
-def train(records, train_idx, steps=3000, lr=3e-3, seed=0, tol_m=3e-6, log=print):
+def train(records, train_idx, steps=3000, lr=3e-3, seed=0, tol_m=3e-6, hidden=64, log=print):
     """Trains the orbital model on the converged runs records[i], i in
     train_idx (full-batch Adam on the device, cosine step size), and the
     eigenvalue model on their eigenvalues.  Returns (orbital Mlp, eigenvalue
@@ -145,7 +161,7 @@ def train(records, train_idx, steps=3000, lr=3e-3, seed=0, tol_m=3e-6, log=print
         eps.append(r["eps"])
     feat, target, wt = torch.cat(feats), torch.cat(targets), torch.cat(wts)
     del feats, targets, wts
-    orb = T.Mlp(W.mlp_init(seed))
+    orb = T.Mlp(W.mlp_init(seed, hidden=hidden), hidden=hidden)
     sched = cosine_lr(lr, steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -161,11 +177,12 @@ def train(records, train_idx, steps=3000, lr=3e-3, seed=0, tol_m=3e-6, log=print
     mfeat = torch.cat(mids)
     et = torch.tensor(np.array(eps, dtype=np.float32), device="cuda")
     ew = torch.full((G,), 1.0 / G, dtype=torch.float32, device="cuda")
-    eig = T.Mlp(W.mlp_init(seed + 1))
+    eig = T.Mlp(W.mlp_init(seed + 1, hidden=hidden), hidden=hidden)
     for k in range(1, steps + 1):
         eig.train_step(mfeat, et, ew, sched(k))
     e_loss = eig.gradient(mfeat, et, ew)[0]
     info = {"points": int(feat.shape[0]), "geometries": G, "steps": steps, "lr": lr, "losses": losses,
+            "hidden": hidden,
             "seconds": t_orb, "ms_per_step": 1e3 * t_orb / steps, "eig_rms": float(np.sqrt(e_loss)),
             "R_range": [min(records[i]["R"] for i in train_idx), max(records[i]["R"] for i in train_idx)]}
     log(f"trained on {info['points']} points of {G} geometries: loss {losses[0][1]:.3e} -> {losses[-1][1]:.3e}, "
@@ -218,10 +235,136 @@ def evaluate(orb, eig, records, test_idx, R_range=None, tol_m=3e-6, tol_scf=1e-4
                "green_iterations": {"superposition": base["gi_steps"], "predicted": warm["gi_steps"]},
                "seconds": {"superposition": base["seconds"], "predicted": warm["seconds"]},
                "e_total": {"superposition": base["e_total"], "predicted": warm["e_total"]},
+               "energy_settled": {"superposition": base["energy_settled"], "predicted": warm["energy_settled"]},
                "converged": bool(base["converged"] and warm["converged"])}
         log(f"R {r['R']:.4f}: orbital error {row['orbital_error']['superposition']:.3e} -> {err_pred:.3e}; "
             f"SCF steps {base['scf_steps']} -> {warm['scf_steps']}, Green iterations {base['gi_steps']} -> "
             f"{warm['gi_steps']}; E {base['e_total']:.7f} / {warm['e_total']:.7f}")
+        rows.append(row)
+    return rows
+
+
+# ------------------------------------------------------ CO: a density model
+# The orbital model needs one well-defined target per orbital; CO's 1pi
+# levels are a degenerate pair that an SCF run may return in any rotation.
+# The density is unique, and Algorithm 1 starts from rho_in, so for CO the
+# network predicts the density: its amplitude sqrt(rho / N_e) as a relative
+# correction of the normalised superposition amplitude s = sqrt(rho_sup / N_e)
+# (the same kernels as the orbital model), rho_warm = N_e psi_warm^2.  The
+# features take the nuclei in list order (C first), so a point's features
+# tell the two atoms apart.  The orbitals keep the aufbau start.
+def generate_co(bond_lengths, tol_m=3e-6, tol_scf=1e-5, log=print):
+    """Converged CO runs from the superposition density and the aufbau
+    orbitals, one per bond length: records (R, n, rho* as float32, E, cost)."""
+    out = []
+    for R in bond_lengths:
+        wl = W.carbon_monoxide_scf(tol_m=tol_m, R=float(R))
+        r = scf_run(wl, tol_scf=tol_scf, max_steps=60)
+        rec = {"R": float(R), "n": wl.n, "w_sum": float(np.sum(wl.mesh.w)), "psi": r["rho"].astype(np.float32),
+               "eps": float(r["eps"][6]), "e_total": float(r["e_total"]), "converged": bool(r["converged"]),
+               "scf_steps": r["scf_steps"], "gi_steps": r["gi_steps"], "seconds": r["seconds"]}
+        log(f"CO R {R:.4f} n {wl.n} E {rec['e_total']:.7f} scf {rec['scf_steps']} gi {rec['gi_steps']} "
+            f"{rec['seconds']:.2f} s")
+        out.append(rec)
+    return out
+
+
+def _co_amplitudes(wl):
+    """(s, features) of a CO workload: the normalised superposition amplitude
+    and the list-order features."""
+    import torch
+
+    from . import tagi as T
+
+    s = np.sqrt(np.maximum(wl.rho, 0.0) / wl.n_elec)
+    feat = T.tagi_mlp_features(_dev(torch, wl.mesh.xyz), wl.meta["nuclei"], ordered=True)
+    return s, feat
+
+
+def train_co(records, train_idx, steps=3000, lr=3e-3, seed=0, tol_m=3e-6, hidden=64, log=print):
+    """The density model on the converged runs records[i], i in train_idx:
+    target sqrt(rho* / rho_sup) - 1, loss sum w s^2 (y - t)^2 =
+    ||s (1 + y) - sqrt(rho* / N_e)||_w^2 before normalisation."""
+    import torch
+
+    from . import tagi as T
+
+    feats, targets, wts = [], [], []
+    G = len(train_idx)
+    for i in train_idx:
+        r = records[i]
+        wl = W.carbon_monoxide_scf(tol_m=tol_m, R=r["R"])
+        if wl.n != r["n"]:
+            raise RuntimeError(f"mesh of R = {r['R']} has {wl.n} points, the record {r['n']}")
+        s, feat = _co_amplitudes(wl)
+        t = np.sqrt(np.maximum(r["psi"].astype(np.float64), 0.0) / np.maximum(wl.rho, 1e-300)) - 1.0
+        feats.append(feat)
+        targets.append(torch.tensor(t.astype(np.float32), device="cuda"))
+        wts.append(torch.tensor((wl.mesh.w * s * s / G).astype(np.float32), device="cuda"))
+    feat, target, wt = torch.cat(feats), torch.cat(targets), torch.cat(wts)
+    del feats, targets, wts
+    model = T.Mlp(W.mlp_init(seed, hidden=hidden), hidden=hidden)
+    sched = cosine_lr(lr, steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = []
+    for k in range(1, steps + 1):
+        want = k == 1 or k % 500 == 0 or k == steps
+        L = model.train_step(feat, target, wt, sched(k), want_loss=want)
+        if want:
+            losses.append((k, L))
+    torch.cuda.synchronize()
+    t_tr = time.perf_counter() - t0
+    info = {"points": int(feat.shape[0]), "geometries": G, "steps": steps, "lr": lr, "losses": losses,
+            "hidden": hidden, "seconds": t_tr, "ms_per_step": 1e3 * t_tr / steps,
+            "R_range": [min(records[i]["R"] for i in train_idx), max(records[i]["R"] for i in train_idx)]}
+    log(f"CO density model: {info['points']} points of {G} geometries, loss {losses[0][1]:.3e} -> "
+        f"{losses[-1][1]:.3e}, {info['ms_per_step']:.2f} ms per step")
+    return model, info
+
+
+def predict_co(model, wl, R_range=None):
+    """rho_warm = N_e psi_warm^2 for a CO workload, or None outside the
+    trained range or when not usable (the superposition density stays)."""
+    import torch
+
+    R = wl.meta["R"]
+    if R_range is not None and not (R_range[0] <= R <= R_range[1]):
+        return None
+    s, feat = _co_amplitudes(wl)
+    psi = model.warm_start(feat, _dev(torch, s), _dev(torch, wl.mesh.w)).cpu().numpy()
+    if not np.all(np.isfinite(psi)):
+        return None
+    return wl.n_elec * psi * psi
+
+
+def evaluate_co(model, records, test_idx, R_range=None, tol_m=3e-6, tol_scf=1e-5, log=print):
+    """SCF runs of the held-out CO geometries from the superposition density
+    and from the predicted one (the same aufbau orbitals)."""
+    rows = []
+    for i in test_idx:
+        r = records[i]
+        wl = W.carbon_monoxide_scf(tol_m=tol_m, R=r["R"])
+        w = wl.mesh.w
+        ref = r["psi"].astype(np.float64)
+        base = scf_run(wl, tol_scf=tol_scf, max_steps=60)
+        rho = predict_co(model, wl, R_range)
+        used = rho is not None
+        warm = scf_run(wl, rho0=rho, tol_scf=tol_scf, max_steps=60) if used else base
+        err = lambda x: float(np.sqrt(np.sum((x - ref) ** 2 * w)))
+        row = {"R": r["R"], "n": wl.n, "used_prediction": used,
+               "density_error": {"superposition": err(wl.rho), "predicted": err(rho) if used else float("nan")},
+               "scf_steps": {"superposition": base["scf_steps"], "predicted": warm["scf_steps"]},
+               "green_iterations": {"superposition": base["gi_steps"], "predicted": warm["gi_steps"]},
+               "seconds": {"superposition": base["seconds"], "predicted": warm["seconds"]},
+               "e_total": {"superposition": base["e_total"], "predicted": warm["e_total"]},
+               "energy_settled": {"superposition": base["energy_settled"], "predicted": warm["energy_settled"]},
+               "converged": bool(base["converged"] and warm["converged"])}
+        es = row["energy_settled"]
+        log(f"CO R {r['R']:.4f}: density error {row['density_error']['superposition']:.3e} -> "
+            f"{row['density_error']['predicted']:.3e}; SCF steps {base['scf_steps']} -> {warm['scf_steps']}; "
+            f"to |dE| < 1e-6: {es['superposition']} -> {es['predicted']}; E {base['e_total']:.7f} / "
+            f"{warm['e_total']:.7f}")
         rows.append(row)
     return rows
 
@@ -232,7 +375,7 @@ def split(count=32):
     return [i for i in range(count) if i not in test], test
 
 
-def profile_case(steps=3):
+def profile_case(steps=3, hidden=64):
     """The kernels of the warm start on one H2 mesh (R = 1.4 Bohr, 192,000
     points): features, `steps` training steps against a smooth synthetic
     target, inference and the warm start.  The command ncu wraps; prints
@@ -247,7 +390,7 @@ def profile_case(steps=3):
     r = np.sqrt((wl.mesh.xyz ** 2).sum(0))
     target = torch.tensor((0.2 * np.tanh(r - 1.0)).astype(np.float32), device="cuda")
     wt = torch.tensor((wl.mesh.w * s * s).astype(np.float32), device="cuda")
-    with T.Mlp(W.mlp_init(0)) as m:
+    with T.Mlp(W.mlp_init(0, hidden=hidden), hidden=hidden) as m:
         m.train_step(feat, target, wt, 1e-3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -258,7 +401,7 @@ def profile_case(steps=3):
         m.forward(feat)
         m.warm_start(feat, _dev(torch, s), _dev(torch, wl.mesh.w))
         torch.cuda.synchronize()
-    print(f"profile case: {wl.n} points, {ms:.3f} ms per training step")
+    print(f"profile case: {wl.n} points, H = {hidden}, {ms:.3f} ms per training step")
 
 
 def main(argv=None):
@@ -274,14 +417,19 @@ def main(argv=None):
     ap.add_argument("--save", default=None, help="write the generated data set here")
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--hidden", type=int, default=64, choices=[32, 64])
+    ap.add_argument("--molecule", default="h2", choices=["h2", "co"])
     ap.add_argument("--profile-case", action="store_true")
     a = ap.parse_args(argv)
     if a.profile_case:
-        profile_case()
+        profile_case(hidden=a.hidden)
         return
     import sys
 
     log = lambda m: print(m, file=sys.stderr, flush=True)
+    if a.molecule == "co":
+        main_co(a, log)
+        return
     Rs = W.h2_bond_lengths()
     t0 = time.perf_counter()
     records = load(a.data) if a.data else generate(Rs, log=log)
@@ -289,11 +437,13 @@ def main(argv=None):
     if a.save and not a.data:
         save(records, a.save)
     tr, te = split(len(records))
-    orb, eig, info = train(records, tr, steps=a.steps, lr=a.lr, log=log)
+    orb, eig, info = train(records, tr, steps=a.steps, lr=a.lr, hidden=a.hidden, log=log)
     rows = evaluate(orb, eig, records, te, R_range=info["R_range"], log=log)
     orb.close()
     eig.close()
     tot = lambda key, k: int(sum(r[key][k] for r in rows))
+    settled = lambda k, f: (sum(r["energy_settled"][k][f] for r in rows)
+                            if all(r["energy_settled"][k] for r in rows) else None)
     out = {"data": {"molecule": "H2", "geometries": len(records), "bond_lengths": [r["R"] for r in records],
                     "points": [r["n"] for r in records], "seconds": t_gen,
                     "all_converged": all(bool(r["converged"]) for r in records)},
@@ -303,7 +453,42 @@ def main(argv=None):
                       "green_iterations": {"superposition": tot("green_iterations", "superposition"),
                                            "predicted": tot("green_iterations", "predicted")},
                       "max_energy_difference": max(abs(r["e_total"]["superposition"] - r["e_total"]["predicted"])
-                                                   for r in rows)}}
+                                                   for r in rows),
+                      "to_energy_settled_1e-6_ha": {
+                          k: {"scf_steps": settled(k, "scf_steps"), "green_iterations": settled(k, "gi_steps"),
+                              "seconds": settled(k, "seconds")} for k in ("superposition", "predicted")}}}
+    print(json.dumps(out))
+
+
+def main_co(a, log):
+    import json
+
+    Rs = W.co_bond_lengths()
+    t0 = time.perf_counter()
+    records = load(a.data) if a.data else generate_co(Rs, log=log)
+    t_gen = time.perf_counter() - t0
+    if a.save and not a.data:
+        save(records, a.save)
+    tr, te = split(len(records))
+    model, info = train_co(records, tr, steps=a.steps, lr=a.lr, hidden=a.hidden, log=log)
+    rows = evaluate_co(model, records, te, R_range=info["R_range"], log=log)
+    model.close()
+    tot = lambda key, k: int(sum(r[key][k] for r in rows))
+    settled = lambda k, f: (sum(r["energy_settled"][k][f] for r in rows)
+                            if all(r["energy_settled"][k] for r in rows) else None)
+    out = {"data": {"molecule": "CO", "geometries": len(records), "bond_lengths": [r["R"] for r in records],
+                    "points": [r["n"] for r in records], "seconds": t_gen,
+                    "all_converged": all(bool(r["converged"]) for r in records)},
+           "train": info, "test": rows,
+           "totals": {"scf_steps": {"superposition": tot("scf_steps", "superposition"),
+                                    "predicted": tot("scf_steps", "predicted")},
+                      "green_iterations": {"superposition": tot("green_iterations", "superposition"),
+                                           "predicted": tot("green_iterations", "predicted")},
+                      "max_energy_difference": max(abs(r["e_total"]["superposition"] - r["e_total"]["predicted"])
+                                                   for r in rows),
+                      "to_energy_settled_1e-6_ha": {
+                          k: {"scf_steps": settled(k, "scf_steps"), "green_iterations": settled(k, "gi_steps"),
+                              "seconds": settled(k, "seconds")} for k in ("superposition", "predicted")}}}
     print(json.dumps(out))
 
 

@@ -519,8 +519,11 @@ def carbon_monoxide(seed: int = 2, tol_m: float = 1e-8, p: int = 4, half_width: 
     return _molecule_workload("CO", mol, mesh, seed, n_orb)
 
 
+CO_BOND = 2.13162  # Bohr: C at (-1.06581, 0, 0), O at (+1.06581, 0, 0) (Section 6)
+
+
 def carbon_monoxide_scf(tol_m: float = 3e-7, p: int = 4, half_width: float = 20.0,
-                        uniform_levels: int = 3) -> Workload:
+                        uniform_levels: int = 3, R: float = CO_BOND) -> Workload:
     """CO for an SCF run from an aufbau-style start: 8 orbitals (7 doubly
     occupied and the 2pi* virtual, N_w = 8 as in Section 6), built from the
     Slater-screened atomic orbitals in energy order and orthonormalised in
@@ -530,8 +533,10 @@ def carbon_monoxide_scf(tol_m: float = 3e-7, p: int = 4, half_width: float = 20.
     V_shift = -1.5: a deeper gauge shift (Eq. gauge-shift leaves the
     eigenproblem unchanged) keeps eps + V_shift < 0 through the first
     gradient-free updates from this crude start.  The tol_m = 3e-7 mesh has
-    638,500 points (the paper's CO mesh at this tolerance: 661,625)."""
-    mol = Molecule(["C", "O"], np.array([[-1.06581, 0.0, 0.0], [1.06581, 0.0, 0.0]]))
+    638,500 points (the paper's CO mesh at this tolerance: 661,625).  R: the
+    bond length (the paper's by default), the nuclei at (-R/2, 0, 0) (C) and
+    (R/2, 0, 0) (O)."""
+    mol = Molecule(["C", "O"], np.array([[-0.5 * R, 0.0, 0.0], [0.5 * R, 0.0, 0.0]]))
     mesh = adaptive_mesh(mol, half_width, p, tol_m, uniform_levels=uniform_levels)
     pts = mesh.xyz.T
     C, O = mol.pos[0], mol.pos[1]
@@ -559,8 +564,15 @@ def carbon_monoxide_scf(tol_m: float = 3e-7, p: int = 4, half_width: float = 20.
     veff = vx + v_hartree0(mol, pts) + lda_xc(rho)[1]
     eps = np.array([-18.8, -9.9, -1.0, -0.5, -0.45, -0.45, -0.35, -0.1])
     return Workload(name="CO", mesh=mesh, veff=veff, psi=np.array(q), eps=eps, rho=rho, vshift=-1.5, theta=0.7,
-                    degree=8, leaf_size=2000, meta={"tol_m": tol_m, "start": "aufbau"}, vext=vx, n_elec=14.0,
+                    degree=8, leaf_size=2000, meta={"tol_m": tol_m, "start": "aufbau", "R": float(R),
+                                                    "nuclei": mol.pos.copy()}, vext=vx, n_elec=14.0,
                     e_zz=nuclear_repulsion(mol))
+
+
+def co_bond_lengths(seed: int = 6, count: int = 32, lo: float = 1.9, hi: float = 2.4) -> np.ndarray:
+    """Seeded CO bond lengths for the density warm-start data set: `count`
+    values drawn uniformly in [lo, hi] Bohr, sorted."""
+    return np.sort(np.random.default_rng(seed).uniform(lo, hi, size=count))
 
 
 def hydrogen_molecule(R: float, tol_m: float = 3e-6, p: int = 4, half_width: float = 20.0,

@@ -53,6 +53,11 @@ def test_argument_validation_needs_no_gpu(lib):
     p = T.make_params(degree=12)
     assert lib.tagi_tree_build(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_int64(10), ctypes.byref(p), None,
                                ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+    for seg in (512, 100000):
+        p = T.make_params(segment=seg)
+        assert lib.tagi_tree_build(ctypes.c_void_p(16), ctypes.c_void_p(16), ctypes.c_int64(10), ctypes.byref(p),
+                                   None, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+        assert "segment" in lib.tagi_last_error().decode()
     assert lib.tagi_tree_destroy(None) == T.TAGI_OK
     lib.tagi_yukawa_conv.argtypes = [ctypes.c_void_p] * 6
     assert lib.tagi_yukawa_conv(None, None, None, 1, None, None) == T.TAGI_ERR_INVALID_ARG
@@ -96,6 +101,9 @@ def test_warm_start_entry_points_validate_without_gpu(lib):
     D = ctypes.POINTER(ctypes.c_double)
     assert L.tagi_mlp_create(7, 32, p.ctypes.data_as(D), p.size, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
     assert L.tagi_mlp_create(8, 64, p.ctypes.data_as(D), p.size, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+    p64 = np.zeros(T.mlp_params(64))
+    assert L.tagi_mlp_create(8, 48, p64.ctypes.data_as(D), p64.size, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
+    assert L.tagi_mlp_create(8, 64, p64.ctypes.data_as(D), p64.size - 1, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
     assert L.tagi_mlp_create(8, 32, p.ctypes.data_as(D), p.size - 1, ctypes.byref(h)) == T.TAGI_ERR_INVALID_ARG
     q = p.copy()
     q[5] = np.nan

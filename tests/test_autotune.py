@@ -10,8 +10,8 @@ import pytest
 from paper_2003_01833_gb300.autotune import Trial, autotune, rel_errors, report, select
 
 
-def _t(n, th, nl, ms, err):
-    return Trial(n, th, nl, 1.0, ms, err, 0)
+def _t(n, th, nl, ms, err, seg=8192):
+    return Trial(n, th, nl, seg, 1.0, ms, err, 0)
 
 
 def test_select_takes_fastest_within_tol():
@@ -31,6 +31,22 @@ def test_select_rejects_nonfinite_and_returns_none():
 
 def test_select_bar_is_inclusive():
     assert select([_t(6, 0.7, 2000, 1.0, 1e-6)], 1e-6) is not None
+
+
+def test_select_across_segment_lengths():
+    trials = [_t(8, 0.7, 2000, 2.0, 4e-7, 8192), _t(8, 0.7, 2000, 1.8, 4.1e-7, 16384),
+              _t(8, 0.7, 2000, 2.2, 4e-7, 4096)]
+    assert select(trials, 1e-6).segment == 16384
+
+
+def test_grid_for_large_meshes_uses_a_narrower_grid_and_fp32c_reference():
+    import paper_2003_01833_gb300.tagi as T
+    from paper_2003_01833_gb300.autotune import grid_for
+
+    small, big = grid_for(300_000), grid_for(1_700_000)
+    assert small == {"segments": (4096, 8192, 16384)}
+    assert big["prec_ref"] == T.TAGI_FP32C and len(big["degrees"]) * len(big["thetas"]) * \
+        len(big["leaf_sizes"]) * len(big["segments"]) == 24
 
 
 def test_rel_errors_plain_and_weighted():
@@ -86,16 +102,22 @@ def test_choice_meets_the_bar_against_direct_sums():
     dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     tol = 1e-6
     best, trials, ref = A.autotune(dev(m.xyz), dev(m.w), dev(f), k, rho=dev(wl.rho), tol=tol, degrees=(6, 8),
-                                   thetas=(0.6, 0.8), leaf_sizes=(1000, 2000))
-    print({(t.degree, t.theta, t.leaf_size): (round(t.conv_ms, 3), f"{t.err_l2:.1e}", f"{t.err_weighted:.1e}")
-           for t in trials})
-    assert len(trials) == 8 and best is not None and best.max_rel_err <= tol
+                                   thetas=(0.6, 0.8), leaf_sizes=(1000, 2000), segments=(4096, 16384))
+    print({(t.degree, t.theta, t.leaf_size, t.segment): (round(t.conv_ms, 3), f"{t.err_l2:.1e}",
+                                                         f"{t.err_weighted:.1e}") for t in trials})
+    assert len(trials) == 16 and best is not None and best.max_rel_err <= tol
+    # the segment length regroups the float32 sums only: the two lengths of
+    # one (n, theta, N_L) agree to float32 accumulation
+    by = {}
+    for t in trials:
+        by.setdefault((t.degree, t.theta, t.leaf_size), []).append(t.err_l2)
+    assert all(abs(a - b) <= 1e-7 for a, b in by.values())
     assert all(t.max_rel_err == t.err_l2 and math.isfinite(t.err_weighted) for t in trials)
     assert all(t.conv_ms >= best.conv_ms for t in trials if t.ok(tol))
     # the chosen configuration against the oracle's direct sums on sampled targets
     tg = np.sort(rng.choice(wl.n, size=3000, replace=False))
     with T.Tree(dev(m.xyz), dev(m.w), theta=best.theta, degree=best.degree, leaf_size=best.leaf_size,
-                prec=T.TAGI_FP32C) as tr:
+                segment=best.segment, prec=T.TAGI_FP32C) as tr:
         u = torch.empty((2, wl.n), dtype=torch.float64, device="cuda")
         vh = torch.empty(wl.n, dtype=torch.float64, device="cuda")
         T.tagi_fields_conv(tr.handle, dev(f), k, u, rho=dev(wl.rho), vh=vh)

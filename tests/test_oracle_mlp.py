@@ -202,3 +202,100 @@ def test_zero_network_warm_start_is_the_superposition_start():
     psi = M.warm_start(np.zeros(M.n_params()), x, s, w)
     np.testing.assert_allclose(psi, s / np.sqrt(np.sum(s * s * w)), rtol=1e-14)
     assert abs(np.sum(psi * psi * w) - 1.0) < 1e-14
+
+
+# ------------------------------------------------- the tensor-core form (H = 64)
+def _bf16_torch(a):
+    """bfloat16 rounding by torch's own cast (float64 -> float32 is exact for
+    these values' 8 significant bits only after rounding, so cast the float64
+    value directly to bfloat16)."""
+    return a.to(torch.bfloat16).to(torch.float64)
+
+
+def test_tensor_core_form_against_autograd_with_straight_through_rounding():
+    """forward_tc and loss_grad_tc against torch: the same network written
+    with torch's bfloat16 cast at each rounding point, differentiated by
+    autograd with the rounding passed straight through (x + (round(x) - x)
+    detached)."""
+    rng = np.random.default_rng(11)
+    H, n = 64, 500
+    p = rng.normal(size=M.n_params(8, H)) * 0.3
+    x = M.bf16_round(rng.normal(size=(n, 8)))
+    t = rng.normal(size=n) * 0.2
+    wt = rng.uniform(0.5, 1.5, size=n)
+    L, g = M.loss_grad_tc(p, x, t, wt, H)
+    y, _ = M.forward_tc(p, x, H)
+    pt = torch.tensor(p, requires_grad=True)
+    o, parts = 0, []
+    for shape in ((H, 8), (H,), (H, H), (H,), (H,), (1,)):
+        k = int(np.prod(shape))
+        parts.append(pt[o:o + k].reshape(shape))
+        o += k
+    W1, b1, W2, b2, W3, b3 = parts
+    st = lambda a: a + (_bf16_torch(a) - a).detach()  # rounded value, identity gradient
+    xt = torch.tensor(x)
+    h1 = torch.tanh(xt @ st(W1).T + b1)
+    h2 = torch.tanh(st(h1) @ st(W2).T + b2)
+    yt = h2 @ st(W3) + b3
+    np.testing.assert_allclose(yt.detach().numpy(), y, rtol=1e-13, atol=1e-15)
+    # the backward pass with its own rounding points, written out by hand
+    r = yt.detach() - torch.tensor(t)
+    dy = 2 * torch.tensor(wt) * r
+    W2r, W3r = _bf16_torch(W2.detach()), _bf16_torch(W3.detach())
+    dz2b = _bf16_torch(dy[:, None] * W3r[None, :] * (1 - h2.detach() ** 2))
+    dz1b = _bf16_torch((dz2b @ W2r) * (1 - h1.detach() ** 2))
+    g_ref = torch.cat([(dz1b.T @ xt).ravel(), dz1b.sum(0), (dz2b.T @ _bf16_torch(h1.detach())).ravel(), dz2b.sum(0),
+                       _bf16_torch(dy) @ _bf16_torch(h2.detach()), _bf16_torch(dy).sum()[None]])
+    # torch's tanh and NumPy's can differ in the last bit, which now and then
+    # moves a value across a bfloat16 rounding boundary: a rare entry
+    # differs by about one bfloat16 unit of one term, every other agrees to
+    # rounding (a misplaced rounding point would move most entries)
+    gr = g_ref.numpy()
+    d = np.abs(g - gr) / np.maximum(np.abs(gr), 1e-300)
+    assert np.mean(d > 1e-10) < 5e-3 and d.max() < 1e-2, (np.mean(d > 1e-10), d.max())
+    # and close to the exact gradient of the rounded-input network: the
+    # rounding points change it by about 2^-8 relative
+    Lt = (torch.tensor(wt) * (yt - torch.tensor(t)) ** 2).sum()
+    Lt.backward()
+    assert abs(Lt.item() - L) < 1e-12 * L
+    rel = np.linalg.norm(g - pt.grad.numpy()) / np.linalg.norm(pt.grad.numpy())
+    assert 1e-5 < rel < 2e-2, rel
+
+
+def test_tensor_core_form_is_the_exact_form_when_rounding_is_exact():
+    """With every activation and gradient value already a bfloat16 number
+    the two forms coincide: a network with W1 = 0 (h1 = tanh(b1), chosen on
+    bfloat16 values of tanh), W3 = 0 and b1, b2 set so that h1 is exact."""
+    H, n = 64, 40
+    rng = np.random.default_rng(3)
+    p = np.zeros(M.n_params(8, H))
+    W1, b1, W2, b2, W3, b3 = M.unpack(p, 8, H)
+    h1_target = M.bf16_round(rng.uniform(-0.5, 0.5, size=H))
+    b1[:] = np.arctanh(h1_target)
+    W2[:] = M.bf16_round(rng.normal(size=(H, H)) * 0.1)
+    b3[:] = 0.25
+    x = M.bf16_round(rng.normal(size=(n, 8)))
+    h1 = np.tanh(b1)
+    assert np.max(np.abs(M.bf16_round(h1) - h1)) < 1e-15  # h1 is a bfloat16 number
+    y_tc, _ = M.forward_tc(p, x, H)
+    y_ex, _ = M.forward(p, x, H)
+    np.testing.assert_allclose(y_tc, y_ex, rtol=0, atol=1e-15)
+
+
+def test_ordered_features_follow_the_list_order():
+    """List-order features of a heteronuclear pair: the same values as the
+    sorted ones where the point is nearer the first nucleus, and r1, r2
+    exchanged where it is nearer the second (so e^-r1 and e^-r2, tanh r1 and
+    tanh r2 swap and (r2 - r1)/R changes sign); R and the symmetric features
+    agree."""
+    nuc = np.array([[-1.0, 0.0, 0.0], [1.2, 0.0, 0.0]])
+    xyz = np.array([[-1.5, 0.3, 0.2], [2.0, -0.4, 0.1], [-1.0, 0.0, 0.0]]).T
+    fo = M.features(xyz, nuc, ordered=True)
+    fs = M.features(xyz, nuc)
+    np.testing.assert_array_equal(fo[0], fs[0])            # nearer the first nucleus
+    np.testing.assert_array_equal(fo[1, [1, 0, 3, 2]], fs[1, [0, 1, 2, 3]])
+    assert fo[1, 4] == -fs[1, 4]
+    np.testing.assert_array_equal(fo[1, 5:], fs[1, 5:])
+    assert fo[2, 0] == 1.0 and fo[2, 2] == 0.0              # on the first nucleus: r1 = 0
+    with pytest.raises(ValueError):
+        M.features(xyz, np.zeros((3, 3)) + np.arange(3)[:, None], ordered=True)

@@ -73,3 +73,18 @@ def test_mlp_init_is_glorot_and_float32():
     assert np.abs(W1).max() <= math.sqrt(6 / 40) and np.abs(W2).max() <= math.sqrt(6 / 64)
     assert np.abs(W3).max() <= math.sqrt(6 / 33)
     assert np.all(p[256:288] == 0) and np.all(p[1312:1344] == 0) and p[-1] == 0
+
+
+def test_co_data_set_geometries():
+    """The CO density data set: 32 seeded bond lengths in [1.9, 2.4] Bohr,
+    held-out ones inside the trained range; the workload puts C and O on the
+    x axis at -R/2 and R/2, and its superposition density integrates to
+    N_e = 14 on the tol_m = 3e-6 mesh."""
+    R = W.co_bond_lengths()
+    assert len(R) == 32 and R.min() >= 1.9 and R.max() <= 2.4 and np.all(np.diff(R) > 0)
+    tr, te = WS.split(32)
+    assert R[tr].min() < R[te].min() and R[te].max() < R[tr].max()
+    wl = W.carbon_monoxide_scf(tol_m=3e-4, R=2.2)
+    np.testing.assert_allclose(wl.meta["nuclei"], [[-1.1, 0, 0], [1.1, 0, 0]])
+    assert wl.meta["R"] == 2.2 and wl.n_elec == 14.0
+    assert abs(np.sum(wl.rho * wl.mesh.w) - 14.0) < 1e-2
