@@ -70,9 +70,14 @@ def scf_run(wl, psi0=None, eps0=None, rho0=None, tol_scf=1e-4, max_steps=40, pre
                                         gi_store_output=store_output) as scf:
         rho, psi, vx = _dev(torch, rho0), _dev(torch, psi0), _dev(torch, wl.vext)
         rep = None
+        error = None
         settled = None  # (steps, Green iterations, seconds) when |dE| < e_tol first held
         for _ in range(max_steps):
-            rep = scf.step(vx, wl.vshift, rho, psi, eps)
+            try:
+                rep = scf.step(vx, wl.vshift, rho, psi, eps)
+            except T.TagiError as e:  # e.g. eps + V_shift >= 0 (Section 3.3): the run has failed
+                error = str(e)
+                break
             eps = rep["eps"]
             hist.append({"residual": rep["residual"], "e_total": rep["e_total"], "gi_steps": rep["gi"]["steps"],
                          "eps": [float(e) for e in eps], "seconds": time.perf_counter() - t0})
@@ -83,7 +88,9 @@ def scf_run(wl, psi0=None, eps0=None, rho0=None, tol_scf=1e-4, max_steps=40, pre
         psi_h = psi.cpu().numpy()
         rho_h = rho.cpu().numpy()
     torch.cuda.synchronize()
-    return {"psi": psi_h, "rho": rho_h, "eps": np.array(eps), "e_total": rep["e_total"], "converged": rep["residual"] < tol_scf,
+    ok = error is None and rep is not None and rep["residual"] < tol_scf
+    return {"psi": psi_h, "rho": rho_h, "eps": np.array(eps), "e_total": rep["e_total"] if rep else float("nan"),
+            "converged": bool(ok), "error": error,
             "scf_steps": len(hist), "gi_steps": int(sum(h["gi_steps"] for h in hist)), "history": hist,
             "seconds": time.perf_counter() - t0,
             "energy_settled": None if settled is None else {"scf_steps": settled[0], "gi_steps": settled[1],
@@ -236,7 +243,8 @@ def evaluate(orb, eig, records, test_idx, R_range=None, tol_m=3e-6, tol_scf=1e-4
                "seconds": {"superposition": base["seconds"], "predicted": warm["seconds"]},
                "e_total": {"superposition": base["e_total"], "predicted": warm["e_total"]},
                "energy_settled": {"superposition": base["energy_settled"], "predicted": warm["energy_settled"]},
-               "converged": bool(base["converged"] and warm["converged"])}
+               "converged": bool(base["converged"] and warm["converged"]),
+               "errors": {"superposition": base["error"], "predicted": warm["error"]}}
         log(f"R {r['R']:.4f}: orbital error {row['orbital_error']['superposition']:.3e} -> {err_pred:.3e}; "
             f"SCF steps {base['scf_steps']} -> {warm['scf_steps']}, Green iterations {base['gi_steps']} -> "
             f"{warm['gi_steps']}; E {base['e_total']:.7f} / {warm['e_total']:.7f}")
@@ -264,7 +272,7 @@ def generate_co(bond_lengths, tol_m=3e-6, tol_scf=1e-5, log=print):
                "eps": float(r["eps"][6]), "e_total": float(r["e_total"]), "converged": bool(r["converged"]),
                "scf_steps": r["scf_steps"], "gi_steps": r["gi_steps"], "seconds": r["seconds"]}
         log(f"CO R {R:.4f} n {wl.n} E {rec['e_total']:.7f} scf {rec['scf_steps']} gi {rec['gi_steps']} "
-            f"{rec['seconds']:.2f} s")
+            f"{rec['seconds']:.2f} s" + ("" if rec["converged"] else f" not converged ({r['error'] or 'step limit'})"))
         out.append(rec)
     return out
 
@@ -359,7 +367,8 @@ def evaluate_co(model, records, test_idx, R_range=None, tol_m=3e-6, tol_scf=1e-5
                "seconds": {"superposition": base["seconds"], "predicted": warm["seconds"]},
                "e_total": {"superposition": base["e_total"], "predicted": warm["e_total"]},
                "energy_settled": {"superposition": base["energy_settled"], "predicted": warm["energy_settled"]},
-               "converged": bool(base["converged"] and warm["converged"])}
+               "converged": bool(base["converged"] and warm["converged"]),
+               "errors": {"superposition": base["error"], "predicted": warm["error"]}}
         es = row["energy_settled"]
         log(f"CO R {r['R']:.4f}: density error {row['density_error']['superposition']:.3e} -> "
             f"{row['density_error']['predicted']:.3e}; SCF steps {base['scf_steps']} -> {warm['scf_steps']}; "
@@ -469,23 +478,30 @@ def main_co(a, log):
     t_gen = time.perf_counter() - t0
     if a.save and not a.data:
         save(records, a.save)
-    tr, te = split(len(records))
+    # geometries whose SCF from the superposition start did not converge are
+    # left out; the split runs over the converged ones in sorted order
+    usable = [i for i, r in enumerate(records) if r["converged"]]
+    tr_u, te_u = split(len(usable))
+    tr, te = [usable[i] for i in tr_u], [usable[i] for i in te_u]
     model, info = train_co(records, tr, steps=a.steps, lr=a.lr, hidden=a.hidden, log=log)
     rows = evaluate_co(model, records, te, R_range=info["R_range"], log=log)
     model.close()
-    tot = lambda key, k: int(sum(r[key][k] for r in rows))
-    settled = lambda k, f: (sum(r["energy_settled"][k][f] for r in rows)
-                            if all(r["energy_settled"][k] for r in rows) else None)
+    both = [r for r in rows if r["converged"]]
+    tot = lambda key, k: int(sum(r[key][k] for r in both))
+    settled = lambda k, f: (sum(r["energy_settled"][k][f] for r in both)
+                            if all(r["energy_settled"][k] for r in both) else None)
     out = {"data": {"molecule": "CO", "geometries": len(records), "bond_lengths": [r["R"] for r in records],
                     "points": [r["n"] for r in records], "seconds": t_gen,
-                    "all_converged": all(bool(r["converged"]) for r in records)},
+                    "all_converged": all(bool(r["converged"]) for r in records),
+                    "converged": [bool(r["converged"]) for r in records]},
            "train": info, "test": rows,
-           "totals": {"scf_steps": {"superposition": tot("scf_steps", "superposition"),
+           "totals": {"rows": len(both),
+                      "scf_steps": {"superposition": tot("scf_steps", "superposition"),
                                     "predicted": tot("scf_steps", "predicted")},
                       "green_iterations": {"superposition": tot("green_iterations", "superposition"),
                                            "predicted": tot("green_iterations", "predicted")},
-                      "max_energy_difference": max(abs(r["e_total"]["superposition"] - r["e_total"]["predicted"])
-                                                   for r in rows),
+                      "max_energy_difference": max((abs(r["e_total"]["superposition"] - r["e_total"]["predicted"])
+                                                    for r in both), default=None),
                       "to_energy_settled_1e-6_ha": {
                           k: {"scf_steps": settled(k, "scf_steps"), "green_iterations": settled(k, "gi_steps"),
                               "seconds": settled(k, "seconds")} for k in ("superposition", "predicted")}}}

@@ -141,7 +141,10 @@ def test_carbon_monoxide_scf_reaches_the_papers_energy(T):
     1e-4: the all-electron LDA energy within 3 mHa of the reference implied
     by Table timings (E_ref = -112.471930 Ha; measured 0.60 mHa, 0.30 mHa per
     atom, in 8 SCF steps; the paper's own run was 0.72 mHa per atom off).
-    The 2pi* level stays empty and the seven below it fully occupied."""
+    The 2pi* level stays empty and the seven below it fully occupied.  The
+    1pi pair (levels 5 and 6) is degenerate by symmetry: its two computed
+    eigenvalues agree to the FP32C eigenvalue accuracy (about 1e-6 Ha per
+    level), in either order, and the levels ascend up to that accuracy."""
     wl = W.carbon_monoxide_scf()
     m = wl.mesh
     with T.Tree(dev(m.xyz), dev(m.w), theta=wl.theta, degree=wl.degree, leaf_size=wl.leaf_size,
@@ -160,7 +163,8 @@ def test_carbon_monoxide_scf_reaches_the_papers_energy(T):
     assert abs(hist[-1][1] - E_REF_CO) < 3e-3
     np.testing.assert_allclose(rep["occ"][:7], 1.0, atol=1e-9)
     assert rep["occ"][7] < 1e-9
-    assert np.all(np.diff(eps) >= -1e-6) and eps[-1] < 0
+    assert abs(eps[4] - eps[5]) < 5e-6
+    assert np.all(np.diff(eps) >= -5e-6) and eps[-1] < 0
 
 
 def test_lithium_scf_with_stored_outputs_reaches_the_papers_energy_closer(T):

@@ -151,10 +151,14 @@ def test_pz_branches_join_smoothly_at_rs_one():
     assert abs(s_lo - s_hi) < 1e-3 * abs(s_hi), (s_lo, s_hi)
 
 
+# treecode of the mesh cases: theta = 0.7, degree 4, leaves of 500 points
+DEG, LEAF = 4, 500
+
+
 @pytest.fixture(scope="module")
 def hmesh():
     wl = W.hydrogen_adaptive()
-    return wl, oracle.Tree(wl.mesh.xyz, 2000)
+    return wl, oracle.Tree(wl.mesh.xyz, LEAF)
 
 
 def test_gaussian_exchange_and_hartree_energies(hmesh):
@@ -166,7 +170,7 @@ def test_gaussian_exchange_and_hartree_energies(hmesh):
     ex, _ = oracle.lda_exchange(rho)
     ex_ref = -(3.0 / 4.0) * (3.0 / np.pi) ** (1 / 3) * N ** (4 / 3) * (a / np.pi) ** 2 * (3 * np.pi / (4 * a)) ** 1.5
     assert abs(np.sum(ex * rho * w) - ex_ref) < 1e-5 * abs(ex_ref)
-    pot = oracle.scf_potentials(T, 0.7, 6, w, np.zeros_like(rho), rho)
+    pot = oracle.scf_potentials(T, 0.7, DEG, w, np.zeros_like(rho), rho)
     eh_ref = N * N * math.sqrt(a / (2 * np.pi))
     assert abs(pot["e_h"] - eh_ref) < 1e-4 * eh_ref
     np.testing.assert_allclose(pot["veff"], pot["vh"] + pot["vxc"], rtol=0, atol=0)
@@ -180,7 +184,7 @@ def test_one_scf_step_of_hydrogen(hmesh):
     psi /= np.sqrt(np.sum(psi * psi * w))
     rho_in = psi * psi
     mix = {}
-    out = oracle.scf_step(T, 0.7, 6, w, -1.0 / r, rho_in, psi[None], np.array([-0.25]), -0.5, 1.0, 6.3336e-4, 0.0,
+    out = oracle.scf_step(T, 0.7, DEG, w, -1.0 / r, rho_in, psi[None], np.array([-0.25]), -0.5, 1.0, 6.3336e-4, 0.0,
                           tol_gi=1e-4, max_iter=30, mix=mix)
     assert out["gi"]["iters"][0] > 0
     assert abs(np.sum(out["rho_out"] * w) - 1.0) < 1e-12
@@ -207,7 +211,7 @@ def test_gradient_free_energy_closed_form_one_electron():
     import scipy.integrate
 
     wl = W.hydrogen_adaptive(tol_m=1e-4)
-    T = oracle.Tree(wl.mesh.xyz, 2000)
+    T = oracle.Tree(wl.mesh.xyz, LEAF)
     w = wl.mesh.w
     r = np.sqrt(np.sum(wl.mesh.xyz**2, axis=0))
     rho = np.exp(-2 * r) / np.pi
@@ -216,8 +220,8 @@ def test_gradient_free_energy_closed_form_one_electron():
     vext = -1.0 / r - vh_exact - vxc
     psi = np.exp(-r) / np.sqrt(np.sum(np.exp(-2 * r) * w))
     e_zz = 0.7
-    out = oracle.scf_step(T, 0.7, 6, w, vext, rho, psi[None], np.array([-0.45]), 0.0, 1.0, 6.3336e-4, e_zz,
-                          tol_gi=1e-6, max_iter=60, mix={})
+    out = oracle.scf_step(T, 0.7, DEG, w, vext, rho, psi[None], np.array([-0.5]), 0.0, 1.0, 6.3336e-4, e_zz,
+                          tol_gi=1e-5, max_iter=60, mix={})
     rad = lambda fn: scipy.integrate.quad(lambda x: 4 * np.pi * x * x * fn(x), 0, 60, limit=400, epsabs=1e-13)[0]
     rho_r = lambda x: np.exp(-2 * x) / np.pi
     e_x = -(81.0 / 256.0) * 3 ** (1 / 3) / np.pi ** (2 / 3)
