@@ -104,6 +104,12 @@ const Tree* as_tree(const tagi_tree* t)
 void ensure_part(Tree& T, int nf)
 {
     T.part.ensure(sizeof(double) * (size_t)T.nitems * nf * kTargetsPerItem);
+    T.tsum.ensure(sizeof(double) * (size_t)(T.ntchunk ? T.ntchunk : 1) * nf * kTargetsPerItem);
+    // the chunk counters must start at zero; the kernels leave them at zero
+    const size_t cb = sizeof(int) * (size_t)(T.ntchunk ? T.ntchunk : 1);
+    const void* before = T.tc_cnt.p;
+    T.tc_cnt.ensure(cb);
+    if (T.tc_cnt.p != before) TAGI_CUDA(cudaMemsetAsync(T.tc_cnt.p, 0, T.tc_cnt.bytes, T.stream));
 }
 
 }  // namespace
@@ -123,7 +129,7 @@ void run_convolution(Tree& T, const double* f, const RateSrc& R, const double* e
             anterpolate_fields32(T, nf);
         }
         ProfScope ps(kProfInteract, T.stream);
-        interact32(T, nf, R.kind, T.rates32.as<float>(), T.part.as<double>());
+        interact32(T, nf, R.kind, T.rates32.as<float>(), T.part.as<double>(), T.tsum.as<double>(), T.tc_cnt.as<int>());
     } else {
         {
             ProfScope ps(kProfAnterp, T.stream);
@@ -133,10 +139,11 @@ void run_convolution(Tree& T, const double* f, const RateSrc& R, const double* e
         ProfScope ps(kProfInteract, T.stream);
         for (int o = 0; o < nf; o++)
             interact64(T, o, nf, R.kind[o], T.rates64.as<double>(), T.q64.as<double>() + (size_t)o * T.nrec,
-                       T.c64.as<double>() + (size_t)o * T.n, T.part.as<double>());
+                       T.c64.as<double>() + (size_t)o * T.n, T.part.as<double>(), T.tsum.as<double>(),
+                       T.tc_cnt.as<int>());
     }
     ProfScope ps(kProfEpilogue, T.stream);
-    reduce_epilogue(T, nf, R.kind, T.part.as<double>(), out);
+    reduce_epilogue(T, nf, R.kind, T.tsum.as<double>(), out);
 }
 
 RateSrc host_rates(const Tree& T, int nf)

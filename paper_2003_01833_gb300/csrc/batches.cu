@@ -23,10 +23,19 @@
 namespace tagi {
 namespace {
 
-__global__ void k_gather_items(const Item* __restrict__ src, const int* __restrict__ idx, int n, Item* dst)
+// dst[i] = src[idx[i]], renumbered into the subset's chunk tables: chunk
+// tcn[i], whose items are [item0[tcn[i]], item0[tcn[i] + 1]).
+__global__ void k_gather_items(const Item* __restrict__ src, const int* __restrict__ idx, const int* __restrict__ tcn,
+                               const int* __restrict__ item0, int n, Item* dst)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[idx[i]];
+    if (i >= n) return;
+    Item it = src[idx[i]];
+    const int c = tcn[i];
+    it.tchunk = c;
+    it.i0 = item0[c];
+    it.ni = item0[c + 1] - item0[c];
+    dst[i] = it;
 }
 
 template <class V>
@@ -62,24 +71,31 @@ struct BatchSubset {
         }
         std::vector<int> pos((size_t)T.nc, -1);
         for (int j = 0; j < T.nleaf; j++) pos[(size_t)leaves[(size_t)j]] = j;
-        std::vector<int> idx, n0, n1, ni0;
+        std::vector<int> idx, tcn, n0, n1, ni0;
         for (int64_t c = 0; c < T.ntchunk; c++) {
             if (!mark[(size_t)pos[(size_t)tb[(size_t)c]]]) continue;
             ni0.push_back((int)idx.size());
             n0.push_back(t0[(size_t)c]);
             n1.push_back(t1[(size_t)c]);
-            for (int it = item0[(size_t)c]; it < item0[(size_t)c + 1]; it++) idx.push_back(it);
+            for (int it = item0[(size_t)c]; it < item0[(size_t)c + 1]; it++) {
+                idx.push_back(it);
+                tcn.push_back((int)n0.size() - 1);
+            }
         }
         ni0.push_back((int)idx.size());
         nitems = (int64_t)idx.size();
         ntchunk = (int64_t)n0.size();
-        DevBuf didx;
+        DevBuf didx, dtcn;
         items.ensure(sizeof(Item) * (size_t)(nitems ? nitems : 1));
         tc_item0.ensure(sizeof(int) * (size_t)(ntchunk + 1));
         tc_t0.ensure(sizeof(int) * (size_t)(ntchunk ? ntchunk : 1));
         tc_t1.ensure(sizeof(int) * (size_t)(ntchunk ? ntchunk : 1));
         didx.ensure(sizeof(int) * (size_t)(nitems ? nitems : 1));
-        if (nitems) TAGI_CUDA(cudaMemcpyAsync(didx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
+        dtcn.ensure(sizeof(int) * (size_t)(nitems ? nitems : 1));
+        if (nitems) {
+            TAGI_CUDA(cudaMemcpyAsync(didx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
+            TAGI_CUDA(cudaMemcpyAsync(dtcn.p, tcn.data(), sizeof(int) * tcn.size(), cudaMemcpyHostToDevice, s));
+        }
         TAGI_CUDA(cudaMemcpyAsync(tc_item0.p, ni0.data(), sizeof(int) * ni0.size(), cudaMemcpyHostToDevice, s));
         if (ntchunk) {
             TAGI_CUDA(cudaMemcpyAsync(tc_t0.p, n0.data(), sizeof(int) * n0.size(), cudaMemcpyHostToDevice, s));
@@ -87,11 +103,12 @@ struct BatchSubset {
         }
         if (nitems) {
             launch(k_gather_items, (int)((nitems + 255) / 256), 256, 0, s, T.items.as<Item>(), didx.as<int>(),
-                   (int)nitems, items.as<Item>());
+                   dtcn.as<int>(), tc_item0.as<int>(), (int)nitems, items.as<Item>());
             TAGI_LAUNCH_CHECK();
         }
         // the host vectors above are pageable: the copies have completed when
-        // cudaMemcpyAsync returns, but the gather must finish before didx goes
+        // cudaMemcpyAsync returns, but the gather must finish before didx and
+        // dtcn go
         TAGI_CUDA(cudaStreamSynchronize(s));
         swap();
     }

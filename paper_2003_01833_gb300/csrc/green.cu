@@ -58,23 +58,21 @@ struct EpiFields {
     EpiField f[kEpiMax];
 };
 
-// One CTA per target chunk: sum the chunk's item partials in item order, add
-// the SS constant and the kernel normalisation, scatter to the caller's order.
+// One CTA per target chunk: the chunk's sum of item partials (formed by the
+// near/far kernel), plus the SS constant and the kernel normalisation,
+// scattered to the caller's order.
 __global__ void k_epilogue(EpiFields E, const double* __restrict__ kvd, int nf_g, int field0, int nf_tot,
-                           const int* __restrict__ tc_item0,
                            const int* __restrict__ tc_t0, const int* __restrict__ tc_t1, const int* __restrict__ perm,
-                           const double* __restrict__ part, const float* __restrict__ c32, int64_t ldc32,
+                           const double* __restrict__ tsum, const float* __restrict__ c32, int64_t ldc32,
                            const double* __restrict__ c64, int64_t n, int ss)
 {
     const int tc = blockIdx.x;
     const int t = tc_t0[tc] + threadIdx.x;
     if (t >= tc_t1[tc]) return;
-    const int i0 = tc_item0[tc], i1 = tc_item0[tc + 1];
     const int dest = perm[t];
     for (int g = 0; g < nf_g; g++) {
         const int o = field0 + g;
-        double S = 0.0;
-        for (int it = i0; it < i1; it++) S += part[((size_t)it * nf_tot + o) * kTargetsPerItem + threadIdx.x];
+        const double S = tsum[((size_t)tc * nf_tot + o) * kTargetsPerItem + threadIdx.x];
         const double c = c32 ? (double)c32[(size_t)o * ldc32 + t] : c64[(size_t)o * n + t];
         const EpiField F = E.f[g];
         const double kv = kvd[o];  // k (Yukawa) or alpha (Coulomb), as the kernel applied them
@@ -233,7 +231,7 @@ void make_rates(Tree& T, const RateSrc& R, const double* eps_dev)
     TAGI_LAUNCH_CHECK();
 }
 
-void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* part, double* const* out)
+void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* tsum, double* const* out)
 {
     const bool fp32 = T.prec == TAGI_FP32C;
     // FP32C: the subtracted sum c_i sum_j G~ w_j carries the mean bias beta of
@@ -251,7 +249,7 @@ void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* part, doub
             E.f[u] = EpiField{out[g0 + u], cf, kind, 0};
         }
         launch(k_epilogue, (int)T.ntchunk, kTargetsPerItem, 0, T.stream, E, (const double*)T.rates64.as<double>(),
-               g, g0, nf, T.tc_item0.as<int>(), T.tc_t0.as<int>(), T.tc_t1.as<int>(), T.perm.as<int>(), part,
+               g, g0, nf, T.tc_t0.as<int>(), T.tc_t1.as<int>(), T.perm.as<int>(), tsum,
                fp32 ? T.fa.as<float>() : nullptr, T.nrec, fp32 ? nullptr : T.c64.as<double>(), T.n, T.ss);
         TAGI_LAUNCH_CHECK();
     }

@@ -396,6 +396,48 @@ __device__ __forceinline__ void tile_near(const float4* __restrict__ sn, int nk,
     }
 }
 
+// Per-chunk sum of the item partials, in the kernel that writes them.  Each
+// CTA stores its partial rows, fences them and counts itself in; the CTA
+// that completes its target chunk's count sums the chunk's rows in item order
+// (the fixed order, so the result does not depend on which CTA finishes
+// last), stores the sum, resets the counter for the next launch, and drops
+// the partial rows' lines from L2 without writing them back: the rows are
+// dead, so they never reach DRAM while they fit in L2 together with the
+// in-flight chunks.  Rows of fields [field0, field0 + nf) of each item are
+// contiguous (nf x 2 KB), so they are whole 128-byte lines.
+__device__ __forceinline__ void discard_line(const void* p)
+{
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
+template <int THREADS>
+__device__ __forceinline__ void chunk_sum(const Item& it, double* __restrict__ part, double* __restrict__ tsum,
+                                          int* __restrict__ cnt, int nf_tot, int field0, int nf)
+{
+    __shared__ int s_last;
+    __threadfence();  // this CTA's partial rows before its count
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(cnt + it.tchunk, 1) == it.ni - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();  // the other CTAs' rows after their counts
+    for (int q = threadIdx.x; q < nf * kTargetsPerItem; q += THREADS) {
+        const int o = field0 + q / kTargetsPerItem, slot = q % kTargetsPerItem;
+        const double* src = part + (size_t)o * kTargetsPerItem + slot;
+        double S = 0.0;
+        for (int i = it.i0; i < it.i0 + it.ni; i++) S += __ldcg(src + (size_t)i * nf_tot * kTargetsPerItem);
+        tsum[((size_t)it.tchunk * nf_tot + o) * kTargetsPerItem + slot] = S;
+    }
+    __syncthreads();  // every read of the rows has returned
+    constexpr int kLineDoubles = 128 / sizeof(double);
+    const int lines = nf * kTargetsPerItem / kLineDoubles;  // per item
+    for (int q = threadIdx.x; q < it.ni * lines; q += THREADS) {
+        const int i = it.i0 + q / lines, l = q % lines;
+        discard_line(part + ((size_t)i * nf_tot + field0) * kTargetsPerItem + (size_t)l * kLineDoubles);
+    }
+    if (threadIdx.x == 0) cnt[it.tchunk] = 0;
+}
+
 // M > 0: approximated clusters use the tensor-grid far path (degree M - 1);
 // M == 0: every entry goes through the record path.
 template <int NY, bool HH, bool SS, int M>
@@ -407,7 +449,8 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
                                                            const float* __restrict__ fa, int64_t lda,
                                                            const float* __restrict__ fb, int64_t ldb,
                                                            const float* __restrict__ kyd,
-                                                           double* __restrict__ part, int nf_tot, int field0)
+                                                           double* __restrict__ part, double* __restrict__ tsum,
+                                                           int* __restrict__ cnt, int nf_tot, int field0)
 {
     constexpr int NF = NY + HH;
     constexpr int G = TileLayout<NF>::G;
@@ -609,6 +652,7 @@ __global__ void __launch_bounds__(Tpt<NY + HH>::threads) k_interact32(const Item
     for (int j = 0; j < TPT; j++)
 #pragma unroll
         for (int o = 0; o < NF; o++) out[o * kTargetsPerItem + tid + j * THREADS] = (double)hi[j][o] + (double)lo[j][o];
+    chunk_sum<THREADS>(it, part, tsum, cnt, nf_tot, field0, NF);
 }
 
 // ---------------------------------------------------------------- bias calibration
@@ -675,6 +719,7 @@ __global__ void __launch_bounds__(kThreads64) k_interact64(const Item* __restric
                                                            const double* __restrict__ rz, const double* __restrict__ rw,
                                                            const double* __restrict__ q, const double* __restrict__ c,
                                                            const double* __restrict__ kvd, double* __restrict__ part,
+                                                           double* __restrict__ tsum, int* __restrict__ cnt,
                                                            int nf_tot, int field)
 {
     const double kval = kvd[field];
@@ -716,52 +761,54 @@ __global__ void __launch_bounds__(kThreads64) k_interact64(const Item* __restric
         }
     }
     part[((size_t)blockIdx.x * nf_tot + field) * kTargetsPerItem + tid] = acc;
+    chunk_sum<kThreads64>(it, part, tsum, cnt, nf_tot, field, 1);
 }
 
 template <int NY, bool HH, bool SS, int M>
-void launch32_m(Tree& T, const float* kyd, const float* q, const float* c, double* part, int nf_tot, int field0)
+void launch32_m(Tree& T, const float* kyd, const float* q, const float* c, double* part, double* tsum, int* cnt,
+                int nf_tot, int field0)
 {
     launch(k_interact32<NY, HH, SS, M>, (int)T.nitems, Tpt<NY + HH>::threads, 0, T.stream, T.items.as<Item>(),
            T.ent.as<Entry>(), T.cl_cen.as<double>(), T.rec4.as<float4>(), T.rec4lo.as<float4>(), q, T.nrec, c, T.n,
-           kyd, part, nf_tot, field0);
+           kyd, part, tsum, cnt, nf_tot, field0);
 }
 
 template <int NY, bool HH>
-void launch32_ss(Tree& T, bool ss, const float* kyd, const float* q, const float* c, double* part, int nf_tot,
-                 int field0)
+void launch32_ss(Tree& T, bool ss, const float* kyd, const float* q, const float* c, double* part, double* tsum,
+                 int* cnt, int nf_tot, int field0)
 {
     // q: rows of fa (fh for points, qh for proxies), c: rows of fb (fl for points).
     // The tensor-grid far path serves degrees 6 and 8 with SS; others take
     // the record path.
     const int m = T.degree + 1;
     if (ss && m == 9)
-        launch32_m<NY, HH, true, 9>(T, kyd, q, c, part, nf_tot, field0);
+        launch32_m<NY, HH, true, 9>(T, kyd, q, c, part, tsum, cnt, nf_tot, field0);
     else if (ss && m == 7)
-        launch32_m<NY, HH, true, 7>(T, kyd, q, c, part, nf_tot, field0);
+        launch32_m<NY, HH, true, 7>(T, kyd, q, c, part, tsum, cnt, nf_tot, field0);
     else if (ss)
-        launch32_m<NY, HH, true, 0>(T, kyd, q, c, part, nf_tot, field0);
+        launch32_m<NY, HH, true, 0>(T, kyd, q, c, part, tsum, cnt, nf_tot, field0);
     else
-        launch32_m<NY, HH, false, 0>(T, kyd, q, c, part, nf_tot, field0);
+        launch32_m<NY, HH, false, 0>(T, kyd, q, c, part, tsum, cnt, nf_tot, field0);
     TAGI_LAUNCH_CHECK();
 }
 
 template <bool HH>
 void launch32_ny(int ny, Tree& T, bool ss, const float* kyd, const float* q, const float* c, double* part,
-                 int nf_tot, int field0)
+                 double* tsum, int* cnt, int nf_tot, int field0)
 {
     switch (ny) {
         case 0:
-            if constexpr (HH) launch32_ss<0, true>(T, ss, kyd, q, c, part, nf_tot, field0);
+            if constexpr (HH) launch32_ss<0, true>(T, ss, kyd, q, c, part, tsum, cnt, nf_tot, field0);
             break;
-        case 1: launch32_ss<1, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
-        case 2: launch32_ss<2, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
-        case 3: launch32_ss<3, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
-        case 4: launch32_ss<4, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
-        case 5: launch32_ss<5, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
-        case 6: launch32_ss<6, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
-        case 7: launch32_ss<7, HH>(T, ss, kyd, q, c, part, nf_tot, field0); break;
+        case 1: launch32_ss<1, HH>(T, ss, kyd, q, c, part, tsum, cnt, nf_tot, field0); break;
+        case 2: launch32_ss<2, HH>(T, ss, kyd, q, c, part, tsum, cnt, nf_tot, field0); break;
+        case 3: launch32_ss<3, HH>(T, ss, kyd, q, c, part, tsum, cnt, nf_tot, field0); break;
+        case 4: launch32_ss<4, HH>(T, ss, kyd, q, c, part, tsum, cnt, nf_tot, field0); break;
+        case 5: launch32_ss<5, HH>(T, ss, kyd, q, c, part, tsum, cnt, nf_tot, field0); break;
+        case 6: launch32_ss<6, HH>(T, ss, kyd, q, c, part, tsum, cnt, nf_tot, field0); break;
+        case 7: launch32_ss<7, HH>(T, ss, kyd, q, c, part, tsum, cnt, nf_tot, field0); break;
         case 8:
-            if constexpr (!HH) launch32_ss<8, false>(T, ss, kyd, q, c, part, nf_tot, field0);
+            if constexpr (!HH) launch32_ss<8, false>(T, ss, kyd, q, c, part, tsum, cnt, nf_tot, field0);
             break;
         default: throw Error(TAGI_ERR_INVALID_ARG, "field group too large");
     }
@@ -818,7 +865,7 @@ double effective_alpha32(double a)
 // at most one Coulomb field (kinds[o] == 1) last.  Groups of at most 8 fields
 // share a launch; the Coulomb field joins the last group when it fits.
 // kyd: device array of the fields' exponent factors (see make_rates).
-void interact32(Tree& T, int nf, const int* kinds, const float* kyd, double* part)
+void interact32(Tree& T, int nf, const int* kinds, const float* kyd, double* part, double* tsum, int* cnt)
 {
     int ny = 0;
     while (ny < nf && kinds[ny] == 0) ny++;
@@ -832,15 +879,15 @@ void interact32(Tree& T, int nf, const int* kinds, const float* kyd, double* par
         const float* q = T.fa.as<float>() + (size_t)o * T.nrec;
         const float* c = T.fb.as<float>() + (size_t)o * T.n;
         if (g_hh)
-            launch32_ny<true>(g_ny, T, T.ss != 0, kyd + o, q, c, part, nf, o);
+            launch32_ny<true>(g_ny, T, T.ss != 0, kyd + o, q, c, part, tsum, cnt, nf, o);
         else
-            launch32_ny<false>(g_ny, T, T.ss != 0, kyd + o, q, c, part, nf, o);
+            launch32_ny<false>(g_ny, T, T.ss != 0, kyd + o, q, c, part, tsum, cnt, nf, o);
         o += g_ny + (g_hh ? 1 : 0);
     }
 }
 
 void interact64(Tree& T, int field, int nf_tot, int kind, const double* kvd, const double* q, const double* c,
-                double* part)
+                double* part, double* tsum, int* cnt)
 {
     const int grid = (int)T.nitems;
     cudaStream_t s = T.stream;
@@ -849,14 +896,14 @@ void interact64(Tree& T, int field, int nf_tot, int kind, const double* kvd, con
     const double *rx = T.rx.as<double>(), *ry = T.ry.as<double>(), *rz = T.rz.as<double>(), *rw = T.rw.as<double>();
     if (kind == 0) {
         if (T.ss)
-            launch(k_interact64<0, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, nf_tot, field);
+            launch(k_interact64<0, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, tsum, cnt, nf_tot, field);
         else
-            launch(k_interact64<0, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, nf_tot, field);
+            launch(k_interact64<0, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, tsum, cnt, nf_tot, field);
     } else {
         if (T.ss)
-            launch(k_interact64<1, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, nf_tot, field);
+            launch(k_interact64<1, true>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, tsum, cnt, nf_tot, field);
         else
-            launch(k_interact64<1, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, nf_tot, field);
+            launch(k_interact64<1, false>, grid, kThreads64, 0, s, it, en, rx, ry, rz, rw, q, c, kvd, part, tsum, cnt, nf_tot, field);
     }
     TAGI_LAUNCH_CHECK();
 }

@@ -122,10 +122,11 @@ struct Entry {
 };
 
 // Work item of the near/far kernel: targets [t0, t1) of batch `batch`
-// (tree positions), list entries [e0, e1).
+// (tree positions), list entries [e0, e1); target chunk `tchunk` of the
+// current chunk tables, whose items are [i0, i0 + ni) of the item array.
 struct Item {
     int t0, t1, e0, e1;
-    int batch, tchunk, pad0, pad1;
+    int batch, tchunk, i0, ni;
 };
 
 // Anterpolation work item: positions [p0, p1) of cluster `cluster`, whose
@@ -191,7 +192,9 @@ struct Tree {
     DevBuf q64;         // double [nf][nrec]
     DevBuf c64;         // double [nf][n] field values in tree order (FP64 SS constants)
     DevBuf wc;          // double [n] quadrature weights in the caller's order
-    DevBuf part;        // double partial sums
+    DevBuf part;        // double partial sums [nitems][nf][kTargetsPerItem]
+    DevBuf tsum;        // double [ntchunk][nf][kTargetsPerItem]: partials summed per target chunk
+    DevBuf tc_cnt;      // int [ntchunk]: items of the chunk finished in the current launch (0 between launches)
     DevBuf antpart;     // double anterpolation partials
     DevBuf antL;        // FP32C: float32 basis rows of every anterpolation point (anterp.cu)
     DevBuf qtiles;      // FP32C: charge tiles of the tensor-core anterpolation (anterp.cu)
@@ -216,9 +219,9 @@ void anterpolate_all_clusters64(Tree& T, const double* q, int nq, double* qh);
 void anterpolate_all_clusters32(Tree& T, const double* q, int nq, double* qh);  // FP32C form (tensor cores)
 // interact.cu
 // kinds[o]: 0 = Yukawa with kval[o], 1 = Coulomb/Hartree
-void interact32(Tree& T, int nf, const int* kinds, const float* kyd, double* part);
+void interact32(Tree& T, int nf, const int* kinds, const float* kyd, double* part, double* tsum, int* cnt);
 void interact64(Tree& T, int field, int nf_tot, int kind, const double* kvd, const double* q, const double* c,
-                double* part);
+                double* part, double* tsum, int* cnt);
 // mean relative bias of the float32 Yukawa and Gaussian kernel values (measured)
 void fp32_bias(cudaStream_t s, double* beta_y, double* beta_g);
 double effective_k32(double k);
@@ -230,7 +233,7 @@ void prepare_points64(Tree& T, const double* f, int nf);   // q64 from caller-or
 void make_rates(Tree& T, const RateSrc& R, const double* eps_dev);
 // u[o][caller i] for o in [0, nf): kinds[o] 0 = Yukawa, 1 = Coulomb, with the
 // rates of the last make_rates.  out[o] points to the caller-order output row.
-void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* part, double* const* out);
+void reduce_epilogue(Tree& T, int nf, const int* kinds, const double* tsum, double* const* out);
 void form_fields(Tree& T, const double* veff, double vshift, const double* psi, int nw, double* f);
 // Green step reductions on caller-order rows, all on the device:
 //   f (nw x n), psi (nw x n, in: old, out: new), u (nw x n, in: Yukawa

@@ -589,13 +589,14 @@ __global__ void k_item_fill(int nleaf, const int* leaves, const int* begin, cons
             acc += padded(ent[e].src1 - ent[e].src0);
             bool last = e + 1 == eoff[j + 1];
             if (acc >= seg_src || last) {
-                if (s < segs) items[first + s] = Item{t0, t1, (int)e0, (int)(e + 1), b, (int)tc, 0, 0};
+                if (s < segs) items[first + s] = Item{t0, t1, (int)e0, (int)(e + 1), b, (int)tc, (int)first, segs};
                 s++;
                 acc = 0;
                 e0 = e + 1;
             }
         }
-        for (; s < segs; s++) items[first + s] = Item{t0, t1, (int)eoff[j + 1], (int)eoff[j + 1], b, (int)tc, 0, 0};
+        for (; s < segs; s++)
+            items[first + s] = Item{t0, t1, (int)eoff[j + 1], (int)eoff[j + 1], b, (int)tc, (int)first, segs};
     }
 }
 
