@@ -617,6 +617,20 @@ BENZENE_H = [(-1.21247, 4.52502), (1.21247, -4.52502), (4.52548, -1.21333), (-4.
              (3.31252, 3.31351), (-3.31252, -3.31351)]
 
 
+def ring_combinations(funcs, angles):
+    """Six functions placed around a hexagonal ring at the given angles ->
+    their six ring combinations, in this order: the sum; the cos and sin of
+    the angle (relative to the first function's) as weights; the cos and sin
+    of twice the angle; alternating signs (cos of three times the angle)."""
+    phi = np.asarray(angles, dtype=np.float64) - float(angles[0])
+    out = [sum(funcs)]
+    for m in (1, 2):
+        out.append(sum(math.cos(m * a) * f for a, f in zip(phi, funcs)))
+        out.append(sum(math.sin(m * a) * f for a, f in zip(phi, funcs)))
+    out.append(sum(math.cos(3 * a) * f for a, f in zip(phi, funcs)))
+    return out
+
+
 def benzene_scf(tol_m: float = 3e-8, p: int = 4, half_width: float = 20.0, uniform_levels: int = 3) -> Workload:
     """C6H6 for an SCF run from an aufbau-style start: 21 orbitals (N_e = 42,
     every level doubly occupied), built from the Slater-screened atomic
@@ -629,6 +643,13 @@ def benzene_scf(tol_m: float = 3e-8, p: int = 4, half_width: float = 20.0, unifo
       3 pi levels: the carbon 2p_z combinations of the lowest Hueckel levels
         of the ring (all in phase, and weighted by the cosine and the sine
         of each carbon's angle around the ring).
+    Each set of six equivalent functions enters as its ring combinations
+    (ring_combinations: weights 1, cos/sin of m times the angle for m = 1, 2,
+    and alternating signs), the symmetry types of the hexagonal ring.  The
+    six 1s levels lie within a few mHa of one another; started from the
+    localised 1s functions, Green Iteration would rotate them toward these
+    combinations at a rate set by that splitting, far too slowly for its
+    per-orbital residual to converge.
     Eigenvalue guesses -9.9 (1s), -0.8 (C-C), -0.6 (C-H), -0.45 and -0.3
     (pi) Ha; V_shift = -1.5 (c31).  The default tol_m = 3e-8 mesh has about
     4.6M points; the paper's Table timings row used tol_m = 3e-6 (1,464,500
@@ -652,14 +673,18 @@ def benzene_scf(tol_m: float = 3e-8, p: int = 4, half_width: float = 20.0, unifo
         r = _dist(pts, R)
         return radial_orbital("2p", z2, r) * (pts[:, 2] - R[2]) / np.maximum(r, 1e-300)
 
-    basis = [radial_orbital("1s", z1, _dist(pts, R)) for R in Cpos]
+    ang = np.arctan2(Cpos[:, 1], Cpos[:, 0])
+    basis = ring_combinations([radial_orbital("1s", z1, _dist(pts, R)) for R in Cpos], ang)
     pairs = [(i, j) for i in range(6) for j in range(i + 1, 6) if np.linalg.norm(Cpos[i] - Cpos[j]) < 3.0]
     assert len(pairs) == 6
-    basis += [hybrid(i, Cpos[j]) + hybrid(j, Cpos[i]) for i, j in pairs]
+    mid = [0.5 * (Cpos[i] + Cpos[j]) for i, j in pairs]
+    basis += ring_combinations([hybrid(i, Cpos[j]) + hybrid(j, Cpos[i]) for i, j in pairs],
+                               np.array([math.atan2(m[1], m[0]) for m in mid]))
+    ch = []
     for i in range(6):
         h = int(np.argmin(np.linalg.norm(Hpos - Cpos[i], axis=1)))
-        basis.append(hybrid(i, Hpos[h]) + radial_orbital("1s", 1.0, _dist(pts, Hpos[h])))
-    ang = np.arctan2(Cpos[:, 1], Cpos[:, 0])
+        ch.append(hybrid(i, Hpos[h]) + radial_orbital("1s", 1.0, _dist(pts, Hpos[h])))
+    basis += ring_combinations(ch, ang)
     basis.append(sum(pz(i) for i in range(6)))
     basis.append(sum(math.cos(ang[i]) * pz(i) for i in range(6)))
     basis.append(sum(math.sin(ang[i]) * pz(i) for i in range(6)))

@@ -122,3 +122,18 @@ def test_lda_potential_is_the_density_derivative():
     # zero density gives zero
     e0, v0 = W.lda_xc(np.zeros(2))
     assert np.all(e0 == 0) and np.all(v0 == 0)
+
+
+def test_ring_combinations_are_the_real_fourier_modes_of_the_ring():
+    """Six functions at angles theta_0 + j pi/3: the combinations' weights
+    are the rows of the real discrete Fourier transform of the ring, which
+    are orthogonal with squared norms 6, 3, 3, 3, 3, 6."""
+    import numpy as np
+
+    from paper_2003_01833_gb300 import workloads as W
+
+    ang = 0.3 + np.arange(6) * np.pi / 3
+    rows = np.array(W.ring_combinations(list(np.eye(6)), ang))
+    np.testing.assert_allclose(rows @ rows.T, np.diag([6.0, 3, 3, 3, 3, 6]), atol=1e-12)
+    np.testing.assert_allclose(rows[0], 1.0)
+    np.testing.assert_allclose(rows[5], [1, -1, 1, -1, 1, -1], atol=1e-12)
