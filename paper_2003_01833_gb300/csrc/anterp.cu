@@ -60,6 +60,90 @@ __device__ __forceinline__ void basis_prod(double t, bool degenerate, int n, con
     }
 }
 
+// Double-float arithmetic for the basis cache: a value is an unevaluated
+// sum h + l of two float32 with |l| <= ulp(h) / 2 (about 48 significant
+// bits).  The error-free sum is Knuth's TwoSum, the product uses the FMA for
+// the exact error of h * h; every step is an explicit round-to-nearest
+// intrinsic so that no contraction changes it.
+struct F2 {
+    float h, l;
+};
+
+__device__ __forceinline__ F2 two_sum_f(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return F2{s, e};
+}
+
+__device__ __forceinline__ F2 df_mul(F2 a, F2 b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);  // exact: a.h * b.h = p + e
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return two_sum_f(p, e);
+}
+
+// (t - s) for a double-float t and a float32 node s
+__device__ __forceinline__ F2 df_sub(F2 t, float s)
+{
+    const F2 d = two_sum_f(t.h, -s);
+    return two_sum_f(d.h, __fadd_rn(d.l, t.l));
+}
+
+__device__ __forceinline__ F2 df_of(double x)
+{
+    const float h = (float)x;
+    return F2{h, (float)(x - (double)h)};
+}
+
+// basis_prod in double-float arithmetic: the same products, with t given as
+// a double-float and the nodes s exact in float32; L[k] is the float32
+// rounding of the result.  float64 runs at about 1/70 of the float32 rate on
+// this GPU; this form costs about a twelfth of the float64 one.
+template <int N>
+__device__ __forceinline__ void basis_df_n(F2 t, const float* s, const F2* inv, float* L)
+{
+    F2 d[N + 1], P[N + 1];
+    F2 pre{1.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k <= N; k++) {
+        d[k] = df_sub(t, s[k]);
+        P[k] = pre;
+        pre = df_mul(pre, d[k]);
+    }
+    F2 suf{1.0f, 0.0f};
+#pragma unroll
+    for (int k = N; k >= 0; k--) {
+        const F2 v = df_mul(P[k], df_mul(suf, inv[k]));
+        L[k] = __fadd_rn(v.h, v.l);
+        suf = df_mul(suf, d[k]);
+    }
+}
+
+__device__ __forceinline__ void basis_df(F2 t, bool degenerate, int n, const float* s, const F2* inv,
+                                         float (&L)[kMaxDegree + 1])
+{
+    if (degenerate) {
+#pragma unroll
+        for (int k = 0; k <= kMaxDegree; k++) L[k] = k == 0 ? 1.0f : 0.0f;
+        return;
+    }
+    switch (n) {  // unrolled per degree, so the products stay in registers
+        case 1: basis_df_n<1>(t, s, inv, L); break;
+        case 2: basis_df_n<2>(t, s, inv, L); break;
+        case 3: basis_df_n<3>(t, s, inv, L); break;
+        case 4: basis_df_n<4>(t, s, inv, L); break;
+        case 5: basis_df_n<5>(t, s, inv, L); break;
+        case 6: basis_df_n<6>(t, s, inv, L); break;
+        case 7: basis_df_n<7>(t, s, inv, L); break;
+        case 8: basis_df_n<8>(t, s, inv, L); break;
+        default: basis_df_n<kMaxDegree>(t, s, inv, L); break;
+    }
+}
+
 constexpr int kAntLP = 12;  // padded basis row of the cache (degree <= 11)
 static_assert(kMaxDegree + 1 <= kAntLP, "basis row fits");
 
@@ -76,10 +160,12 @@ __host__ __device__ inline size_t antl_index(size_t item, int j, int d, int k)
 }
 
 // Basis cache of the float32 path: for every point of every anterpolation
-// item and each dimension, the float64 basis of Eq. Lagrange_polynomials on
-// the float32-rounded nodes, rounded to float32 (exactly the values k_ant
-// evaluates), in the tile layout of antl_index; the points of the last tile
-// beyond the item's end hold zeros.
+// item and each dimension, the basis of Eq. Lagrange_polynomials on the
+// float32-rounded nodes at the float64 scaled coordinate, evaluated in
+// double-float arithmetic (basis_df) and rounded to float32 (the float32
+// rounding of the float64 basis except where a value lies within about
+// 1e-13 of a rounding boundary), in the tile layout of antl_index; the
+// points of the last tile beyond the item's end hold zeros.
 __global__ void __launch_bounds__(kAntThreads) k_ant_basis(const AntItem* __restrict__ items,
                                                            const double* __restrict__ px,
                                                            const double* __restrict__ py,
@@ -89,6 +175,8 @@ __global__ void __launch_bounds__(kAntThreads) k_ant_basis(const AntItem* __rest
                                                            float* __restrict__ antL)
 {
     __shared__ double dnodes[kMaxDegree + 1], inv[kMaxDegree + 1];
+    __shared__ float fnodes[kMaxDegree + 1];
+    __shared__ F2 finv[kMaxDegree + 1];
     const AntItem it = items[blockIdx.x];
     const int c = it.cluster;
     double cc[3], hh[3], ih[3];
@@ -104,6 +192,8 @@ __global__ void __launch_bounds__(kAntThreads) k_ant_basis(const AntItem* __rest
             for (int j = 0; j <= degree; j++)
                 if (j != k) d *= dnodes[k] - dnodes[j];
             inv[k] = 1.0 / d;
+            fnodes[k] = (float)dnodes[k];
+            finv[k] = df_of(inv[k]);
         }
     }
     __syncthreads();
@@ -114,12 +204,16 @@ __global__ void __launch_bounds__(kAntThreads) k_ant_basis(const AntItem* __rest
     for (int e = threadIdx.x; e < ntile * 3 * kTcK; e += blockDim.x) {
         const int jj = e & 31, rest = e >> 5, d = rest % 3, j = (rest / 3) * kTcK + jj;
         const double* x = d == 0 ? px : (d == 1 ? py : pz);
-        const bool deg = hh[d] == 0.0;
-        double Ld[kMaxDegree + 1];
-        if (j < np) basis_prod(deg ? 0.0 : (x[it.p0 + j] - cc[d]) * ih[d], deg, degree, dnodes, inv, Ld);
+        // (select, not index: a runtime index would put the arrays in local memory)
+        const double ccd = d == 0 ? cc[0] : (d == 1 ? cc[1] : cc[2]);
+        const double hhd = d == 0 ? hh[0] : (d == 1 ? hh[1] : hh[2]);
+        const double ihd = d == 0 ? ih[0] : (d == 1 ? ih[1] : ih[2]);
+        const bool deg = hhd == 0.0;
+        float Lf[kMaxDegree + 1];
+        if (j < np) basis_df(df_of(deg ? 0.0 : (x[it.p0 + j] - ccd) * ihd), deg, degree, fnodes, finv, Lf);
 #pragma unroll
         for (int k = 0; k < kAntLP; k++)
-            antL[antl_index(blockIdx.x, j, d, k)] = (j < np && k <= degree && k <= kMaxDegree) ? (float)Ld[k] : 0.0f;
+            antL[antl_index(blockIdx.x, j, d, k)] = (j < np && k <= degree && k <= kMaxDegree) ? Lf[k] : 0.0f;
     }
 }
 
