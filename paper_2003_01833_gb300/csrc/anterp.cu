@@ -324,6 +324,76 @@ __global__ void __launch_bounds__(kAntThreads) k_ant(const AntItem* __restrict__
     }
 }
 
+// w^ of the FP32C tree from the two-float weight columns (w_hi, w_lo) and
+// the basis cache, in proxy pencils: thread t < M^2 owns the M proxies
+// (k1, k2, k3 = 0 .. M-1) with k1 = t / M, k2 = t % M.  L1 L2 is formed once
+// per point and pencil and the k3 values are broadcast from shared memory,
+// so a point costs 2 + M + 2 shared loads per pencil instead of 5 per proxy
+// (k_ant is bound by its shared loads).  The products, (L1 L2) L3 times each
+// column, and the summation order (float sums over 64-point tiles in point
+// order, float64 across tiles) are those of k_ant, so w^ is bit-identical.
+template <int M>
+struct Pencil {
+    static constexpr int threads = (M * M + 31) / 32 * 32;
+};
+
+template <int M>
+__global__ void __launch_bounds__(Pencil<M>::threads) k_ant_pencil(const AntItem* __restrict__ items,
+                                                                   const float* __restrict__ q, int64_t ldq,
+                                                                   double* __restrict__ part,
+                                                                   const float* __restrict__ antL)
+{
+    constexpr int P = M * M * M;
+    __shared__ float Ls[kAntTile][3][M];
+    __shared__ float qs[2][kAntTile];
+    const AntItem it = items[blockIdx.x];
+    const int t = threadIdx.x;
+    const bool own = t < M * M;
+    const int k1 = own ? t / M : 0, k2 = own ? t % M : 0;
+    double acc[M][2];
+#pragma unroll
+    for (int k = 0; k < M; k++) acc[k][0] = acc[k][1] = 0.0;
+    for (int p0 = it.p0; p0 < it.p1; p0 += kAntTile) {
+        const int nt = min(kAntTile, it.p1 - p0);
+        __syncthreads();
+        for (int e = t; e < kAntTile * 3 * M; e += Pencil<M>::threads) {
+            const int j = e / (3 * M), d = (e / M) % 3, k = e % M;
+            Ls[j][d][k] = j < nt ? antL[antl_index(blockIdx.x, (p0 - it.p0) + j, d, k)] : 0.0f;
+        }
+        for (int e = t; e < 2 * kAntTile; e += Pencil<M>::threads) {
+            const int col = e / kAntTile, j = e % kAntTile;
+            qs[col][j] = j < nt ? q[col * ldq + p0 + j] : 0.0f;
+        }
+        __syncthreads();
+        float tacc[M][2];
+#pragma unroll
+        for (int k = 0; k < M; k++) tacc[k][0] = tacc[k][1] = 0.0f;
+        for (int j = 0; j < nt; j++) {
+            const float l12 = Ls[j][0][k1] * Ls[j][1][k2];
+            const float q0 = qs[0][j], q1 = qs[1][j];
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                const float L = l12 * Ls[j][2][k];
+                tacc[k][0] += L * q0;
+                tacc[k][1] += L * q1;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+            acc[k][0] += (double)tacc[k][0];
+            acc[k][1] += (double)tacc[k][1];
+        }
+    }
+    if (!own) return;
+    double* out = part + (size_t)blockIdx.x * 2 * P;
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+        const int pk = (k1 * M + k2) * M + k;
+        out[pk] = acc[k][0];
+        out[P + pk] = acc[k][1];
+    }
+}
+
 // ---------------------------------------------------------------- tensor cores
 constexpr int kTcFormWarps = 8;                      // warps that form operands and fold
 constexpr int kTcThreads = 32 * (kTcFormWarps + 1);  // + one warp that issues MMAs and bulk copies
@@ -785,8 +855,15 @@ void anterpolate_weights(Tree& T)
         DevBuf w2;
         w2.ensure(sizeof(float) * 2 * (size_t)T.n);
         launch(k_split_w, (int)((T.n + 255) / 256), 256, 0, s, T.pw.as<double>(), T.n, w2.as<float>());
-        launch_ant<float, double>(2, (int)T.nant, T.ant_items.as<AntItem>(), T, w2.as<float>(), T.n,
-                                  T.antpart.as<double>(), s, antL);
+        if (antL && T.degree == 8)
+            launch(k_ant_pencil<9>, (int)T.nant, Pencil<9>::threads, 0, s, T.ant_items.as<AntItem>(), w2.as<float>(),
+                   T.n, T.antpart.as<double>(), antL);
+        else if (antL && T.degree == 6)
+            launch(k_ant_pencil<7>, (int)T.nant, Pencil<7>::threads, 0, s, T.ant_items.as<AntItem>(), w2.as<float>(),
+                   T.n, T.antpart.as<double>(), antL);
+        else
+            launch_ant<float, double>(2, (int)T.nant, T.ant_items.as<AntItem>(), T, w2.as<float>(), T.n,
+                                      T.antpart.as<double>(), s, antL);
         launch(k_ant_reduce_w, T.nfar, 256, 0, s, T.far_ant0.as<int>(), T.antpart.as<double>(), T.P, T.n,
                T.rec4.as<float4>());
         TAGI_LAUNCH_CHECK();
