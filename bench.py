@@ -388,7 +388,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(wl), "segment": seg or 8192, "model": "oracle treecode (float64 CPU)"},
+           "config": {"workload": workload_name(wl), "model": "oracle treecode (float64 CPU)"},
            "cpu_baseline": {"kind": "oracle", "value": v, "unit": UNIT, "cores": smp.threads, "sample": desc},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -90,3 +90,30 @@ def test_workload_names_match_between_arms(bench):
     wl = W.hydrogen_1s()
     assert bench.workload_name(wl) == bench.workload_name(wl)
     assert f"{wl.n} points" in bench.workload_name(wl)
+
+
+def test_reference_arm_prints_its_line(bench, capsys):
+    """bench.py --impl reference (the oracle on the host cores) on the small
+    Li mesh: one JSON line with the keys the comparison of the two arms reads,
+    the same workload string as the GPU arm, and the oracle thread count put
+    back afterwards."""
+    import argparse
+    import json
+
+    import oracle
+
+    before = oracle.threads()
+    saved = bench.WORKLOAD
+    try:
+        bench.WORKLOAD = "li-small"
+        bench.run_reference(argparse.Namespace(gpus=1, steps=1, warmup=0))
+    finally:
+        bench.WORKLOAD = saved
+        oracle.threads(before)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == bench.UNIT
+    assert line["metric"] == bench.METRIC and line["higher_is_better"] is True
+    assert line["config"]["workload"].startswith("Li atom") and "99000 points" in line["config"]["workload"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
