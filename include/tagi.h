@@ -472,7 +472,9 @@ tagi_status tagi_scf_destroy(tagi_scf* scf);
  * distances to the two nearest nuclei (lower index first on ties) and R the
  * distance between those two nuclei,
  *   [e^-r1, e^-r2, tanh r1, tanh r2, (r2 - r1)/R, tanh((r1 + r2)/R - 1),
- *    R - 1.5, e^-(r1 + r2 - R)].
+ *    R - 1.5, e^-(r1 + r2 - R)]
+ * (with per-nucleus decay rates z1, z2 the first two are e^-(z1 r1) and
+ * e^-(z2 r2): tagi_mlp_features_scaled).
  * ------------------------------------------------------------------------ */
 typedef struct tagi_mlp tagi_mlp;
 typedef struct {
@@ -499,6 +501,15 @@ tagi_status tagi_mlp_features(const double* xyz, int64_t n, const double* nuclei
  * nuclei [host] 2*3 positions, distinct. */
 tagi_status tagi_mlp_features_ordered(const double* xyz, int64_t n, const double* nuclei, uint16_t* feat,
                                       void* stream);
+/* The features with a decay rate per nucleus in the first two: e^-(z1 r1)
+ * and e^-(z2 r2), z1 and z2 the rates of the nuclei at distances r1 and r2
+ * (all 1: tagi_mlp_features / _ordered, bit for bit).  A rate near the
+ * Slater exponent of a heavier atom's 1s shell resolves its core, where the
+ * rate-1 exponentials are nearly flat.  scale [host] n_nuclei rates, finite
+ * and > 0; ordered: 0 (two nearest, 2..16 nuclei) or 1 (list order, 2
+ * nuclei).  TAGI_ERR_INVALID_ARG for a NULL scale or a bad rate. */
+tagi_status tagi_mlp_features_scaled(const double* xyz, int64_t n, const double* nuclei, const double* scale,
+                                     int n_nuclei, int ordered, uint16_t* feat, void* stream);
 /* y [dev] n float32 out: the network's output for each point. */
 tagi_status tagi_mlp_forward(const tagi_mlp* mlp, const uint16_t* feat, int64_t n, float* y, void* stream);
 /* Loss L = sum_p wt_p (y_p - t_p)^2 and dL/dparams of the current master

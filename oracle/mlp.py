@@ -12,7 +12,8 @@ Definitions (F = 8 features, H hidden units, tanh):
 - features of a point x with nearest nuclei at distances r1 <= r2 and
   separation R of those two nuclei:
   [e^-r1, e^-r2, tanh r1, tanh r2, (r2 - r1)/R, tanh((r1 + r2)/R - 1),
-   R - 1.5, e^-(r1 + r2 - R)], each rounded to bfloat16;
+   R - 1.5, e^-(r1 + r2 - R)], each rounded to bfloat16 (with a decay rate
+  z per nucleus the first two are e^-(z1 r1) and e^-(z2 r2));
 - parameters, in this order: W1 (H x F), b1 (H), W2 (H x H), b2 (H),
   W3 (H), b3 (1); the weights W1, W2, W3 enter the products rounded to
   bfloat16, the biases unrounded;
@@ -55,10 +56,12 @@ def unpack(params, F: int = N_FEATURES, H: int = 32):
     return out
 
 
-def features(xyz, nuclei, ordered: bool = False):
+def features(xyz, nuclei, ordered: bool = False, scale=None):
     """xyz (3, n), nuclei (m, 3) with m >= 2: the bfloat16-rounded features
     (n, 8) of the definition above.  ordered (m = 2 only): r1 and r2 are the
-    distances to the first and the second nucleus of the list, unsorted."""
+    distances to the first and the second nucleus of the list, unsorted.
+    scale (m,): a decay rate z per nucleus; the first two features are then
+    e^-(z1 r1) and e^-(z2 r2) with z1, z2 the rates of the nuclei at r1, r2."""
     xyz = np.asarray(xyz, dtype=np.float64)
     nuc = np.asarray(nuclei, dtype=np.float64).reshape(-1, 3)
     if nuc.shape[0] < 2 or (ordered and nuc.shape[0] != 2):
@@ -72,9 +75,12 @@ def features(xyz, nuclei, ordered: bool = False):
         i1, i2 = order[:, 0], order[:, 1]
     rows = np.arange(d.shape[0])
     r1, r2 = d[rows, i1], d[rows, i2]
+    z = np.ones(nuc.shape[0]) if scale is None else np.asarray(scale, dtype=np.float64).ravel()
+    if z.size != nuc.shape[0] or not np.all(np.isfinite(z) & (z > 0)):
+        raise ValueError("one finite positive decay rate per nucleus")
     R = np.sqrt(((nuc[i1] - nuc[i2]) ** 2).sum(axis=1))
-    f = np.stack([np.exp(-r1), np.exp(-r2), np.tanh(r1), np.tanh(r2), (r2 - r1) / R, np.tanh((r1 + r2) / R - 1.0),
-                  R - 1.5, np.exp(-(r1 + r2 - R))], axis=1)
+    f = np.stack([np.exp(-z[i1] * r1), np.exp(-z[i2] * r2), np.tanh(r1), np.tanh(r2), (r2 - r1) / R,
+                  np.tanh((r1 + r2) / R - 1.0), R - 1.5, np.exp(-(r1 + r2 - R))], axis=1)
     return bf16_round(f)
 
 

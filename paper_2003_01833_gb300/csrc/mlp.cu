@@ -42,6 +42,7 @@ constexpr size_t kGradSmem = sizeof(float) * (kPPad + (size_t)kThreads * kStride
 
 struct Nuclei {
     double x[kMaxNuclei], y[kMaxNuclei], z[kMaxNuclei];
+    double zs[kMaxNuclei];  // decay rate of each nucleus's exponential features (1 by default)
     int m;
     int ordered;  // 1: two nuclei taken in list order (r1 to the first) instead of by distance
 };
@@ -108,8 +109,9 @@ __device__ __forceinline__ float layer2_unit(const float* sw, const float h1[kH]
 
 // ------------------------------------------------------------------ kernels
 // Features of a point (float64, rounded once to bfloat16): with r1 <= r2 the
-// distances to the two nearest nuclei (the lower index first on ties) and R
-// their separation, [e^-r1, e^-r2, tanh r1, tanh r2, (r2 - r1)/R,
+// distances to the two nearest nuclei (the lower index first on ties), z1
+// and z2 those nuclei's decay rates (1 unless given) and R their
+// separation, [e^-(z1 r1), e^-(z2 r2), tanh r1, tanh r2, (r2 - r1)/R,
 // tanh((r1 + r2)/R - 1), R - 1.5, e^-(r1 + r2 - R)].  Sums of squares are
 // formed left to right without contraction.
 __global__ void k_features(const double* __restrict__ xyz, int64_t n, Nuclei nuc, uint16_t* __restrict__ feat)
@@ -141,8 +143,8 @@ __global__ void k_features(const double* __restrict__ xyz, int64_t n, Nuclei nuc
     const double ex = nuc.x[a1] - nuc.x[a2], ey = nuc.y[a1] - nuc.y[a2], ez = nuc.z[a1] - nuc.z[a2];
     const double R = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
     const double s12 = __dadd_rn(d1, d2);
-    const double f[kF] = {exp(-d1),
-                          exp(-d2),
+    const double f[kF] = {exp(-__dmul_rn(nuc.zs[a1], d1)),
+                          exp(-__dmul_rn(nuc.zs[a2], d2)),
                           tanh(d1),
                           tanh(d2),
                           __dsub_rn(d2, d1) / R,
@@ -526,8 +528,8 @@ tagi_status tagi_mlp_get_params(const tagi_mlp* mlp, double* params, int64_t n_p
     });
 }
 
-static tagi_status features_call(const double* xyz, int64_t n, const double* nuclei, int n_nuclei, int ordered,
-                          uint16_t* feat, void* stream)
+static tagi_status features_call(const double* xyz, int64_t n, const double* nuclei, const double* scale,
+                                 int n_nuclei, int ordered, uint16_t* feat, void* stream)
 {
     return guarded_mlp([&] {
         TAGI_REQUIRE(xyz != nullptr && nuclei != nullptr, "xyz or nuclei is NULL");
@@ -541,8 +543,10 @@ static tagi_status features_call(const double* xyz, int64_t n, const double* nuc
             nu.x[a] = nuclei[3 * a];
             nu.y[a] = nuclei[3 * a + 1];
             nu.z[a] = nuclei[3 * a + 2];
+            nu.zs[a] = scale ? scale[a] : 1.0;
             TAGI_REQUIRE(std::isfinite(nu.x[a]) && std::isfinite(nu.y[a]) && std::isfinite(nu.z[a]),
                          "nuclei must be finite");
+            TAGI_REQUIRE(std::isfinite(nu.zs[a]) && nu.zs[a] > 0.0, "decay rates must be finite and positive");
         }
         for (int a = 0; a < n_nuclei; a++)
             for (int b = 0; b < a; b++)
@@ -556,13 +560,20 @@ static tagi_status features_call(const double* xyz, int64_t n, const double* nuc
 tagi_status tagi_mlp_features(const double* xyz, int64_t n, const double* nuclei, int n_nuclei, uint16_t* feat,
                               void* stream)
 {
-    return features_call(xyz, n, nuclei, n_nuclei, 0, feat, stream);
+    return features_call(xyz, n, nuclei, nullptr, n_nuclei, 0, feat, stream);
 }
 
 tagi_status tagi_mlp_features_ordered(const double* xyz, int64_t n, const double* nuclei, uint16_t* feat,
                                       void* stream)
 {
-    return features_call(xyz, n, nuclei, 2, 1, feat, stream);
+    return features_call(xyz, n, nuclei, nullptr, 2, 1, feat, stream);
+}
+
+tagi_status tagi_mlp_features_scaled(const double* xyz, int64_t n, const double* nuclei, const double* scale,
+                                     int n_nuclei, int ordered, uint16_t* feat, void* stream)
+{
+    if (!scale) return report_error(TAGI_ERR_INVALID_ARG, "scale is NULL");
+    return features_call(xyz, n, nuclei, scale, n_nuclei, ordered ? 1 : 0, feat, stream);
 }
 
 tagi_status tagi_mlp_forward(const tagi_mlp* mlp, const uint16_t* feat, int64_t n, float* y, void* stream)

@@ -142,6 +142,8 @@ def lib():
         L.tagi_mlp_features.argtypes = [_vp, ctypes.c_int64, _D, ctypes.c_int, _vp, _vp]
         L.tagi_mlp_features_ordered.argtypes = [_vp, ctypes.c_int64, _D, _vp, _vp]
         L.tagi_mlp_features_ordered.restype = ctypes.c_int
+        L.tagi_mlp_features_scaled.argtypes = [_vp, ctypes.c_int64, _D, _D, ctypes.c_int, ctypes.c_int, _vp, _vp]
+        L.tagi_mlp_features_scaled.restype = ctypes.c_int
         L.tagi_mlp_forward.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
         L.tagi_mlp_gradient.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _D, _D, _vp]
         L.tagi_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(tagi_adam_params),
@@ -612,10 +614,11 @@ def _tptr(t, name, dtype, numel):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def tagi_mlp_features(xyz, nuclei, feat=None, stream=None, ordered=False):
+def tagi_mlp_features(xyz, nuclei, feat=None, stream=None, ordered=False, scale=None):
     """xyz (3, n) float64 CUDA; nuclei (m, 3) host positions.  Returns the
     (n, 8) bfloat16 encodings as an int16 CUDA tensor (feat if given).
-    ordered: two nuclei in list order (tagi_mlp_features_ordered)."""
+    ordered: two nuclei in list order (tagi_mlp_features_ordered); scale:
+    m decay rates of the first two features (tagi_mlp_features_scaled)."""
     import torch
 
     n = xyz.numel() // 3
@@ -623,7 +626,14 @@ def tagi_mlp_features(xyz, nuclei, feat=None, stream=None, ordered=False):
     if feat is None:
         feat = torch.empty((n, MLP_FEATURES), dtype=torch.int16, device=xyz.device)
     fp = _tptr(feat, "feat", torch.int16, n * MLP_FEATURES)
-    if ordered:
+    if scale is not None:
+        zs = np.ascontiguousarray(np.asarray(scale, dtype=np.float64).ravel())
+        if zs.size != nu.shape[0]:
+            raise ValueError("one decay rate per nucleus")
+        _check(lib().tagi_mlp_features_scaled(_dptr(xyz, "xyz", 3 * n), n, nu.ctypes.data_as(_D),
+                                              zs.ctypes.data_as(_D), nu.shape[0], int(bool(ordered)), fp,
+                                              _stream(stream)))
+    elif ordered:
         if nu.shape[0] != 2:
             raise ValueError("list order needs exactly two nuclei")
         _check(lib().tagi_mlp_features_ordered(_dptr(xyz, "xyz", 3 * n), n, nu.ctypes.data_as(_D), fp,

@@ -277,22 +277,29 @@ def generate_co(bond_lengths, tol_m=3e-6, tol_scf=1e-5, log=print):
     return out
 
 
+# decay rates of the first two CO features: the Slater 1s exponents of C and
+# O (the nuclei in list order), so that those features resolve the two cores
+CO_FEATURE_RATES = (W.ATOM_Z["C"] - 0.30, W.ATOM_Z["O"] - 0.30)
+
+
 def _co_amplitudes(wl):
     """(s, features) of a CO workload: the normalised superposition amplitude
-    and the list-order features."""
+    and the list-order features with the 1s decay rates of C and O."""
     import torch
 
     from . import tagi as T
 
     s = np.sqrt(np.maximum(wl.rho, 0.0) / wl.n_elec)
-    feat = T.tagi_mlp_features(_dev(torch, wl.mesh.xyz), wl.meta["nuclei"], ordered=True)
+    feat = T.tagi_mlp_features(_dev(torch, wl.mesh.xyz), wl.meta["nuclei"], ordered=True, scale=CO_FEATURE_RATES)
     return s, feat
 
 
 def train_co(records, train_idx, steps=3000, lr=3e-3, seed=0, tol_m=3e-6, hidden=64, log=print):
     """The density model on the converged runs records[i], i in train_idx:
-    target sqrt(rho* / rho_sup) - 1, loss sum w s^2 (y - t)^2 =
-    ||s (1 + y) - sqrt(rho* / N_e)||_w^2 before normalisation."""
+    target t = sqrt(rho* / rho_sup) - 1, with rho = N_e s^2 (1 + y)^2 the
+    predicted density.  The loss is the density error to first order in
+    y - t: sum w (2 N_e s^2 (1 + t))^2 (y - t)^2 ~ ||rho - rho*||_w^2, the
+    norm the held-out comparison reports."""
     import torch
 
     from . import tagi as T
@@ -305,10 +312,14 @@ def train_co(records, train_idx, steps=3000, lr=3e-3, seed=0, tol_m=3e-6, hidden
         if wl.n != r["n"]:
             raise RuntimeError(f"mesh of R = {r['R']} has {wl.n} points, the record {r['n']}")
         s, feat = _co_amplitudes(wl)
-        t = np.sqrt(np.maximum(r["psi"].astype(np.float64), 0.0) / np.maximum(wl.rho, 1e-300)) - 1.0
+        rho_c = np.maximum(r["psi"].astype(np.float64), 0.0)  # the converged density of the record
+        # the target, bounded where both densities vanish (its weight is ~0 there)
+        t = np.clip(np.sqrt(rho_c / np.maximum(wl.rho, 1e-300)) - 1.0, -1.0, 100.0)
         feats.append(feat)
         targets.append(torch.tensor(t.astype(np.float32), device="cuda"))
-        wts.append(torch.tensor((wl.mesh.w * s * s / G).astype(np.float32), device="cuda"))
+        # (2 N_e s^2 (1 + t))^2 = 4 rho_sup rho*: finite wherever the target is large
+        wts.append(torch.tensor((wl.mesh.w * 4.0 * np.maximum(wl.rho, 0.0) * rho_c / G).astype(np.float32),
+                                device="cuda"))
     feat, target, wt = torch.cat(feats), torch.cat(targets), torch.cat(wts)
     del feats, targets, wts
     model = T.Mlp(W.mlp_init(seed, hidden=hidden), hidden=hidden)

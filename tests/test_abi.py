@@ -117,6 +117,11 @@ def test_warm_start_entry_points_validate_without_gpu(lib):
     assert L.tagi_mlp_features(fake, 10, nuc.ctypes.data_as(D), 2, ctypes.c_void_p(18), None) \
         == T.TAGI_ERR_INVALID_ARG  # feat not 16-byte aligned
     assert L.tagi_mlp_features(fake, 0, nuc.ctypes.data_as(D), 2, fake, None) == T.TAGI_ERR_INVALID_ARG
+    zs = np.array([5.7, 0.0])
+    assert L.tagi_mlp_features_scaled(fake, 10, nuc.ctypes.data_as(D), zs.ctypes.data_as(D), 2, 1, fake, None) \
+        == T.TAGI_ERR_INVALID_ARG  # a rate must be positive
+    assert L.tagi_mlp_features_scaled(fake, 10, nuc.ctypes.data_as(D), None, 2, 1, fake, None) \
+        == T.TAGI_ERR_INVALID_ARG
     assert L.tagi_mlp_forward(None, fake, 10, fake, None) == T.TAGI_ERR_INVALID_ARG
     a = T.tagi_adam_params(1e-3, 0.9, 0.999, 1e-8)
     assert L.tagi_mlp_train_step(None, fake, fake, fake, 10, ctypes.byref(a), None, None) == T.TAGI_ERR_INVALID_ARG

@@ -80,6 +80,13 @@ def test_ordered_features_bit_exact(T):
     xyz[:, :2] = nuc.T
     f = as_values(T.tagi_mlp_features(dev(xyz), nuc, ordered=True))
     np.testing.assert_array_equal(f, M.features(xyz, nuc, ordered=True))
+    z = [5.7, 7.7]  # Slater 1s exponents of C and O
+    f = as_values(T.tagi_mlp_features(dev(xyz), nuc, ordered=True, scale=z))
+    np.testing.assert_array_equal(f, M.features(xyz, nuc, ordered=True, scale=z))
+    nuc3 = np.array([[-0.7, 0.0, 0.0], [0.7, 0.0, 0.0], [0.3, 2.1, -0.4]])
+    z3 = [1.0, 2.5, 4.0]
+    f = as_values(T.tagi_mlp_features(dev(xyz), nuc3, scale=z3))
+    np.testing.assert_array_equal(f, M.features(xyz, nuc3, scale=z3))
 
 
 def test_forward_against_oracle(T):

@@ -299,3 +299,26 @@ def test_ordered_features_follow_the_list_order():
     assert fo[2, 0] == 1.0 and fo[2, 2] == 0.0              # on the first nucleus: r1 = 0
     with pytest.raises(ValueError):
         M.features(xyz, np.zeros((3, 3)) + np.arange(3)[:, None], ordered=True)
+
+
+def test_scaled_features_closed_forms():
+    """Decay rates per nucleus: the first two features become e^-(z1 r1) and
+    e^-(z2 r2) for the rates of the nuclei at r1 and r2, in closed form at
+    the second nucleus and on the bond axis; rates of 1 give the plain
+    features bit for bit; the other six features do not change."""
+    R = 2.1
+    nuc = np.array([[-R / 2, 0, 0], [R / 2, 0, 0]])
+    z = np.array([5.7, 7.7])
+    b = M.bf16_round
+    pts = np.array([[R / 2, 0, 0], [-R / 2 - 0.3, 0, 0], [0.1, 0.4, -0.2]]).T
+    f = M.features(pts, nuc, ordered=True, scale=z)
+    assert f[0, 0] == b(math.exp(-z[0] * R)) and f[0, 1] == 1.0   # on the second nucleus: r2 = 0
+    assert f[1, 0] == b(math.exp(-z[0] * 0.3)) and f[1, 1] == b(math.exp(-z[1] * (R + 0.3)))
+    plain = M.features(pts, nuc, ordered=True)
+    np.testing.assert_array_equal(f[:, 2:], plain[:, 2:])
+    np.testing.assert_array_equal(M.features(pts, nuc, scale=[1.0, 1.0]), M.features(pts, nuc))
+    # nearest-pair order: the rate follows the nucleus, not the slot
+    s = M.features(pts, nuc, scale=z)
+    assert s[0, 0] == 1.0 and s[0, 1] == b(math.exp(-z[0] * R))
+    with pytest.raises(ValueError):
+        M.features(pts, nuc, scale=[1.0, 0.0])
