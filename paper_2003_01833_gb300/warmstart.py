@@ -395,6 +395,14 @@ def split(count=32):
     return [i for i in range(count) if i not in test], test
 
 
+def split_converged(records):
+    """split() over the records whose SCF converged (the others are left
+    out): (train, test) indices into records, in sorted order."""
+    usable = [i for i, r in enumerate(records) if r["converged"]]
+    tr_u, te_u = split(len(usable))
+    return [usable[i] for i in tr_u], [usable[i] for i in te_u]
+
+
 def profile_case(steps=3, hidden=64):
     """The kernels of the warm start on one H2 mesh (R = 1.4 Bohr, 192,000
     points): features, `steps` training steps against a smooth synthetic
@@ -489,11 +497,7 @@ def main_co(a, log):
     t_gen = time.perf_counter() - t0
     if a.save and not a.data:
         save(records, a.save)
-    # geometries whose SCF from the superposition start did not converge are
-    # left out; the split runs over the converged ones in sorted order
-    usable = [i for i, r in enumerate(records) if r["converged"]]
-    tr_u, te_u = split(len(usable))
-    tr, te = [usable[i] for i in tr_u], [usable[i] for i in te_u]
+    tr, te = split_converged(records)
     model, info = train_co(records, tr, steps=a.steps, lr=a.lr, hidden=a.hidden, log=log)
     rows = evaluate_co(model, records, te, R_range=info["R_range"], log=log)
     model.close()

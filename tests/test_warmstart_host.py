@@ -88,3 +88,15 @@ def test_co_data_set_geometries():
     np.testing.assert_allclose(wl.meta["nuclei"], [[-1.1, 0, 0], [1.1, 0, 0]])
     assert wl.meta["R"] == 2.2 and wl.n_elec == 14.0
     assert abs(np.sum(wl.rho * wl.mesh.w) - 14.0) < 1e-2
+
+
+def test_split_leaves_out_runs_that_did_not_converge():
+    """The CO data set keeps only converged SCF runs; every fourth of those
+    (in sorted order, starting with the second) is held out."""
+    from paper_2003_01833_gb300 import warmstart as WS
+
+    conv = [True, False, True, True, True, False, True, True, True, True]
+    tr, te = WS.split_converged([{"converged": c} for c in conv])
+    usable = [i for i, c in enumerate(conv) if c]  # 0 2 3 4 6 7 8 9
+    assert te == [usable[1], usable[5]] == [2, 7]
+    assert sorted(tr + te) == usable and not set(tr) & set(te)
